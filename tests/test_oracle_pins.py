@@ -1,0 +1,153 @@
+"""Pins the C oracles to facts fixed by mathematics, not to themselves.
+
+- axpy + sum: the closed form of the x[i]=i, y[i]=1 input (every partial sum is
+  exact in binary64), line count and file bytes;
+- exact sum: Python's math.fsum (Shewchuk's exactly rounded summation) on data
+  with heavy cancellation, plus hand cases (overflowing naive sums, ties to
+  even, subnormals);
+- Jacobi: separable eigenmodes of the discrete Laplacian with Dirichlet
+  boundary decay by a known factor per sweep (anisotropic, so a swapped axis or
+  stride changes the factor), and single spikes checked by hand.
+"""
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2306_11686_gb300 import inputs
+
+
+def run(cmd, **kw):
+    p = subprocess.run(cmd, capture_output=True, text=True, **kw)
+    assert p.returncode == 0, p.stderr
+    return p.stdout
+
+
+# ------------------------------------------------------------------ axpy_sum
+
+def test_axpy_closed_form(oracle_bin, tmp_path):
+    n = 4096 + 17
+    x, y = inputs.axpy_closed_form_inputs(n)
+    inputs.write_f64(tmp_path / "x.bin", x)
+    inputs.write_f64(tmp_path / "y.bin", y)
+    out = run([oracle_bin("axpy_sum"), str(n), tmp_path / "x.bin", tmp_path / "y.bin", tmp_path / "o.bin"])
+    lines = out.splitlines()
+    assert len(lines) == (n + 1023) // 1024 + 1
+    for ln in lines[:-1]:
+        i, v = ln.split()
+        assert float(v) == 2.5 * int(i) + 1.0          # y_new = 2.5 x + y with x=i, y=1
+    assert lines[-1] == "sum %.17g" % (2.5 * n * (n - 1) / 2 + n)
+    got = np.fromfile(tmp_path / "o.bin", dtype=np.float64)
+    assert np.array_equal(got, 2.5 * np.arange(n) + 1.0)
+
+
+def test_axpy_random_matches_elementwise_definition(oracle_bin, tmp_path):
+    n = 3000
+    x, y = inputs.axpy_inputs(n, seed=7)
+    inputs.write_f64(tmp_path / "x.bin", x)
+    inputs.write_f64(tmp_path / "y.bin", y)
+    out = run([oracle_bin("axpy_sum"), str(n), tmp_path / "x.bin", tmp_path / "y.bin", tmp_path / "o.bin"])
+    want = (2.5 * x) + y                                 # two roundings, no fused multiply-add
+    got = np.fromfile(tmp_path / "o.bin", dtype=np.float64)
+    assert np.array_equal(got, want)
+    first = out.splitlines()[0]
+    assert first == "0 %.17g" % want[0]
+    s = float(out.splitlines()[-1].split()[1])
+    assert abs(s - math.fsum(want)) <= 1e-12 * abs(math.fsum(want))
+
+
+# ------------------------------------------------------------------ exact_sum
+
+def exact(oracle_bin, tmp_path, arr):
+    p = tmp_path / "s.bin"
+    np.asarray(arr, dtype=np.float64).tofile(p)
+    vals = dict(l.split() for l in run([oracle_bin("exact_sum"), p]).splitlines())
+    return {k: float(v) for k, v in vals.items()}
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_exact_sum_matches_fsum_with_cancellation(oracle_bin, tmp_path, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal(5000) * 10.0 ** rng.integers(-20, 20, 5000)
+    a = np.concatenate([a, -a[:2500] * (1 + 1e-15)])  # heavy cancellation
+    rng.shuffle(a)
+    r = exact(oracle_bin, tmp_path, a)
+    assert r["exact"] == math.fsum(a)
+    assert r["absum"] == math.fsum(np.abs(a))
+
+
+def test_exact_sum_hand_cases(oracle_bin, tmp_path):
+    r = exact(oracle_bin, tmp_path, [1e308, 1e308, -1e308])
+    assert r["exact"] == 1e308 and math.isinf(r["naive"])
+    assert exact(oracle_bin, tmp_path, [1.0, 2.0 ** -53])["exact"] == 1.0              # tie, to even
+    assert exact(oracle_bin, tmp_path, [1.0, 2.0 ** -53, 2.0 ** -106])["exact"] == 1.0 + 2.0 ** -52
+    assert exact(oracle_bin, tmp_path, [5e-324, 5e-324, 5e-324])["exact"] == 1.5e-323
+    assert exact(oracle_bin, tmp_path, [-3.5, 1.25, -0.75])["exact"] == -3.0
+    assert exact(oracle_bin, tmp_path, [0.1] * 10)["exact"] == math.fsum([0.1] * 10)
+
+
+# ------------------------------------------------------------------ jacobi
+
+def jacobi(oracle_bin, tmp_path, grid, n, sweeps):
+    inputs.write_f64(tmp_path / "in.bin", grid)
+    out = run([oracle_bin("jacobi"), str(n), str(sweeps), tmp_path / "in.bin", tmp_path / "out.bin"])
+    res = [(int(a), float(b)) for a, b in (l.split() for l in out.splitlines())]
+    return res, np.fromfile(tmp_path / "out.bin", dtype=np.float64).reshape(n, n, n)
+
+
+def mode(n, a, b, c):
+    t = np.arange(n) * np.pi / (n - 1)
+    g = np.einsum("k,j,i->kji", np.sin(c * t), np.sin(b * t), np.sin(a * t))
+    g[0], g[-1], g[:, 0], g[:, -1], g[:, :, 0], g[:, :, -1] = 0, 0, 0, 0, 0, 0
+    return g
+
+
+@pytest.mark.parametrize("abc", [(1, 1, 1), (1, 2, 3), (3, 1, 2)])
+def test_jacobi_eigenmode_decay(oracle_bin, tmp_path, abc):
+    n, sweeps = 18, 4
+    g0 = mode(n, *abc)
+    lam = sum(math.cos(m * math.pi / (n - 1)) for m in abc) / 3.0
+    res, g = jacobi(oracle_bin, tmp_path, g0.reshape(-1), n, sweeps)
+    assert [s for s, _ in res] == list(range(1, sweeps + 1))
+    assert np.max(np.abs(g - lam ** sweeps * g0)) <= 1e-13
+    m0 = np.max(np.abs(g0))
+    for s, r in res:
+        want = abs(lam) ** (s - 1) * abs(1 - lam) * m0
+        assert abs(r - want) <= 1e-13 + 1e-12 * want
+
+
+def test_jacobi_single_spike(oracle_bin, tmp_path):
+    n = 8
+    g0 = np.zeros((n, n, n))
+    g0[4, 4, 4] = 6.0
+    res, g = jacobi(oracle_bin, tmp_path, g0.reshape(-1), n, 1)
+    want = np.zeros((n, n, n))
+    for d in [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]:
+        want[4 + d[0], 4 + d[1], 4 + d[2]] = 1.0
+    assert np.array_equal(g, want)
+    assert res == [(1, 6.0)]
+
+
+def test_jacobi_spike_next_to_boundary(oracle_bin, tmp_path):
+    n = 6
+    g0 = np.zeros((n, n, n))
+    g0[1, 2, 3] = 3.0                                   # (k, j, i)
+    res, g = jacobi(oracle_bin, tmp_path, g0.reshape(-1), n, 1)
+    want = np.zeros((n, n, n))
+    for k, j, i in [(2, 2, 3), (1, 1, 3), (1, 3, 3), (1, 2, 2), (1, 2, 4)]:  # (0,2,3) is boundary
+        want[k, j, i] = 0.5
+    assert np.array_equal(g, want)
+    assert res == [(1, 3.0)]
+
+
+def test_jacobi_boundary_zero_and_random_grid(oracle_bin, tmp_path):
+    n = 12
+    g0 = inputs.jacobi_input(n, seed=2).reshape(n, n, n)
+    res, g = jacobi(oracle_bin, tmp_path, g0.reshape(-1), n, 3)
+    for face in (g[0], g[-1], g[:, 0], g[:, -1], g[:, :, 0], g[:, :, -1]):
+        assert not face.any()
+    # max principle: the average of neighbours stays within the range of the previous sweep
+    assert g.max() <= g0.max() and g.min() >= 0.0
+    assert all(r > 0 for _, r in res)
