@@ -1,0 +1,253 @@
+"""Benchmark: the legacy 3-D Jacobi program run whole on the GPU.
+
+Workload (one step = one complete program run through the C ABI):
+  256^3 FP64 grid, interior ~ U[0,1) (seed 2), zero Dirichlet boundary,
+  100 sweeps; each sweep takes a fresh grid from the device heap and frees
+  the old one, fuses the max-residual reduction into the stencil region and
+  prints one line over RPC; the final grid is fwrite'd (copy-engine DMA).
+
+metric  loop GB/s: algorithmic loop bytes of the whole program (per sweep:
+        read the grid once, write the new grid once = 2 * 8 * 256^3 B)
+        divided by the device time of the whole program (CUDA events on the
+        launch stream around gf_run_main).
+e2e     same metric through the same call with a HOST input buffer (the
+        loader's H2D copy inside the timed region) and the program's fwrite
+        of the result to a file (D2H) inside it.
+
+--impl reference times the serial C oracle of the same program on the host
+cores (a bounded sample of sweeps per step) under the same metric.
+"""
+import argparse
+import json
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, SWEEPS = 256, 100
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def loop_bytes(n, sweeps):
+    return 2 * 8 * n ** 3 * sweeps
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples SM clock and throttle reasons with nvidia-smi during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.rows, self.proc = [], None
+
+    def __enter__(self):
+        if shutil.which("nvidia-smi"):
+            dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", dev, f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 3 + k and r[3 + k].lower().startswith("active")})
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def cpu_oracle_sample(n, sweeps, tmp):
+    """Times the serial C oracle (1 thread) on `sweeps` sweeps of the same grid."""
+    import numpy as np
+    from oracle import build as ob
+    from paper_2306_11686_gb300 import inputs
+    ob.build()
+    path = os.path.join(tmp, "in.bin")
+    if not os.path.exists(path):
+        inputs.write_f64(path, inputs.jacobi_input(n, seed=2))
+    t0 = time.perf_counter()
+    subprocess.run([ob.binary("jacobi"), str(n), str(sweeps), path, os.path.join(tmp, "ref.bin")],
+                   check=True, stdout=subprocess.DEVNULL)
+    dt = time.perf_counter() - t0
+    return loop_bytes(n, sweeps) / dt / 1e9, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    tmp = tempfile.mkdtemp(prefix="gfbench")
+    sample = max(1, args.ref_sweeps)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(N, sample, tmp)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt = cpu_oracle_sample(N, sample, tmp)
+        vals.append(v)
+        times.append(dt)
+    v = sum(loop_bytes(N, sample) for _ in times) / sum(times) / 1e9
+    line = {"impl": "reference", "metric": "loop GB/s (% HBM peak)", "value": round(v, 3), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * sum(times) / len(times), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"jacobi-7pt {N}^3 fp64, {sample} sweeps per step (bounded sample of 100)",
+                       "l2": "grid larger than L2"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{sample} sweeps of {N}^3 per step"},
+            "e2e": {"value": round(v, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    shutil.rmtree(tmp, ignore_errors=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gf", choices=["gf", "reference"])
+    ap.add_argument("--ref-sweeps", type=int, default=4)
+    ap.add_argument("--cpu-sweeps", type=int, default=8)
+    ap.add_argument("--out-dir", default=None, help="where the program writes its final grid")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_2306_11686_gb300 import gf, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    tmp = tempfile.mkdtemp(prefix="gfbench", dir=args.out_dir)
+    out_path = os.path.join(tmp, f"grid_r{rank}.bin")
+
+    g = inputs.jacobi_input(N, seed=2)
+    gd = torch.from_numpy(g).to(dev)
+    gh = torch.from_numpy(g).pin_memory()
+    stream = torch.cuda.Stream(device=dev)
+    heap = 3 * N ** 3 * 8 + (256 << 20)
+    ctx = gf.Context(stream=stream, heap_bytes=heap, heap_small_pct=5,
+                     stdout_path=os.path.join(tmp, f"stdout_r{rank}.txt"))
+    argv = [N, SWEEPS, out_path]
+
+    def step(buf):
+        rc, ec = ctx.run("jacobi", argv, [(buf, gf.GF_BUF_IN)])
+        if ec != 0:
+            raise RuntimeError(f"jacobi exit code {ec}")
+
+    for _ in range(args.warmup):
+        step(gd)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- value: inputs resident in HBM
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    with Clocks() as clk:
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            step(gd)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    per = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    total = sum(per)
+    if world > 1:
+        t = torch.tensor([total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = t.item()
+    st = ctx.stats()
+    value = loop_bytes(N, SWEEPS) * args.steps * world / total / 1e9
+
+    # ---- e2e: host input staged in by the loader, result written by the program's fwrite
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        step(gh)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_t = e0.elapsed_time(e1) / 1e3
+    e2e = loop_bytes(N, SWEEPS) * e2e_steps * world / e2e_t / 1e9
+
+    peak, peak_kind = hbm_peak()
+    achieved = loop_bytes(N, SWEEPS) / (total / args.steps) / 1e9
+    cpu = None
+    if rank == 0:
+        cv, cdt = cpu_oracle_sample(N, args.cpu_sweeps, tmp)
+        cpu = {"value": round(cv, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sweeps} sweeps of the {N}^3 grid ({cdt:.2f} s)"}
+    if rank == 0:
+        line = {
+            "metric": "loop GB/s (% HBM peak)", "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"jacobi-7pt {N}^3 fp64, {SWEEPS} sweeps, per-sweep device malloc/free, "
+                                   "fused max-residual, printf per sweep, final fwrite",
+                       "grid": st.grid, "block": st.block, "l2": "inputs larger than L2 (2 x 134 MB grids)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_kind": peak_kind, "kernel": "program_kernel<jacobi>"},
+            "e2e": {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": N ** 3 * 8,
+                    "d2h_bytes_per_step": N ** 3 * 8 + 100 * 24},
+            "gpu_launches": args.steps,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "detail": {"main_ns": st.main_ns, "regions": st.regions, "rpc_p50_ns": st.rpc_p50_ns,
+                       "rpc_p99_ns": st.rpc_p99_ns, "rpc_wait_ns": st.rpc_wait_ns,
+                       "step_s": [round(p, 6) for p in per]},
+        }
+        print(json.dumps(line))
+    ctx.close()
+    shutil.rmtree(tmp, ignore_errors=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

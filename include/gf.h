@@ -1,0 +1,184 @@
+/*
+ * gf.h -- C ABI of the GPU-First runtime for GB300 (sm_103a).
+ *
+ * What the library does (paper: "GPU First -- Execution of Legacy CPU Codes on
+ * GPUs", Sec. 1 and Sec. 3, Fig. 1): a legacy-style program runs WHOLE on one
+ * GPU.  Its serial part runs on one initial thread, its parallel-for regions
+ * are workshared over every SM (Sec. 3.3), malloc/free are served by a device
+ * heap (Sec. 3.4) and libc calls the GPU cannot make (printf, fopen, fwrite,
+ * fread, fclose, clock, getenv) are forwarded to a host server by RPC
+ * (Sec. 3.2).  Programs are written against the device header gf_device.cuh
+ * and registered by name with GF_MAIN(name); this header is the host side.
+ *
+ * Conventions for every function below:
+ *  - return 0 (GF_OK) on success or a negative GF_E* code; nothing aborts;
+ *  - pointers are plain host pointers unless the argument says "device";
+ *    a cudaStream_t travels as void*;
+ *  - the context owns every buffer it allocates; caller buffers stay the
+ *    caller's.  Functions are thread-safe per context unless noted.
+ */
+#ifndef GF_H
+#define GF_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GF_API __attribute__((visibility("default")))
+#else
+#define GF_API
+#endif
+
+/* ------------------------------------------------------------------ errors */
+#define GF_OK 0
+#define GF_EINVAL -1       /* bad argument, unknown handle, record larger than a ring slot  */
+#define GF_ENOMEM -2       /* device heap, ring or host allocation exhausted                */
+#define GF_ERING -3        /* no ring slot became free within the timeout                   */
+#define GF_ETIMEDOUT -4    /* the host (or a region / barrier) did not answer in time       */
+#define GF_EHOST -5        /* a host landing pad failed                                     */
+#define GF_ECUDA -6        /* a CUDA runtime call failed                                    */
+#define GF_ENOENT -7       /* no program registered under that name                         */
+#define GF_EBUSY -8        /* no free program instance (admission refused)                  */
+
+/* ------------------------------------------------------------------ types */
+typedef struct gf_ctx gf_ctx;          /* runtime context: ring, heap, server, instances   */
+typedef struct gf_handle gf_handle;    /* one launched program                             */
+typedef int32_t gf_program;            /* registry id from gf_program_lookup               */
+
+/* Runtime configuration.  Fill with gf_config_default, then override. */
+typedef struct gf_config {
+    uint64_t heap_bytes;          /* device heap arena per program instance (default 4 GiB)        */
+    uint32_t heap_small_pct;      /* percent of the arena for the small-size slabs (default 50)    */
+    uint32_t ring_slots;          /* ring slots per program instance, power of two (default 4096)  */
+    uint32_t slot_bytes;          /* bytes per slot, multiple of 64, >= 1024 (default 4096)        */
+    uint32_t aggregate;           /* 1 = warp-aggregated RPC, 0 = one slot per calling thread      */
+    uint32_t server_threads;      /* host RPC server threads started by gf_init (default 1;
+                                     0 = the caller serves with gf_rpc_serve / gf_wait)            */
+    uint32_t max_programs;        /* program instances that may run at once (default 1)           */
+    uint32_t grid;                /* blocks per program launch, 0 = SMs x occupancy / max_programs */
+    int64_t timeout_ns;           /* bound of every device wait (default 30 s)                     */
+    void *stream;                 /* cudaStream_t for gf_run_main (NULL = a stream of the context) */
+    const char *stdout_path;      /* where device printf goes (NULL = this process's stdout)       */
+    uint32_t fmt_cache;           /* format-string cache entries per instance, power of two (4096) */
+    int32_t device;               /* CUDA device ordinal (-1 = current device)                    */
+} gf_config;
+
+/* A buffer mapped into the program before main (the loader's job, paper
+ * Sec. 3.1).  Device pointers are used in place.  Host pointers are copied to
+ * device memory before launch when dir has GF_BUF_IN and copied back after the
+ * program ends when dir has GF_BUF_OUT.  The program reads them with
+ * gf_buffer(i) / gf_buffer_bytes(i). */
+#define GF_BUF_IN 1u
+#define GF_BUF_OUT 2u
+typedef struct gf_buf {
+    void *ptr;
+    uint64_t bytes;
+    uint32_t dir;
+    uint32_t pad;
+} gf_buf;
+
+/* Counters of the last program waited for on this context (host fields
+ * accumulate over the context's life). */
+#define GF_NOPS 16
+typedef struct gf_stats {
+    uint64_t rpc_calls[GF_NOPS];  /* lane records per opcode (index = GF_OP_*)               */
+    uint64_t rpc_slots[GF_NOPS];  /* ring slots per opcode (calls / slots = aggregation)    */
+    uint64_t rpc_wait_ns;         /* device time leaders spent waiting for the host        */
+    double rpc_p50_ns;            /* device round-trip latency percentiles (claim -> done) */
+    double rpc_p99_ns;
+    uint64_t regions;             /* parallel regions run                                   */
+    uint64_t heap_alloc, heap_free, heap_fail, heap_bad_free;
+    uint64_t heap_live_bytes, heap_high_water;
+    uint64_t main_ns;             /* device time from main() entry to return               */
+    uint64_t host_slots;          /* slots the host served (cumulative)                    */
+    uint64_t host_records;        /* lane records the host served (cumulative)             */
+    uint64_t host_ns;             /* host time inside landing pads (cumulative)            */
+    uint64_t host_dma_bytes;      /* bytes moved by DMA for fwrite/fread (cumulative)      */
+    int32_t grid, block;          /* launch shape of the last program                      */
+    int32_t error;                /* first device-side error of the last program           */
+    int32_t exit_code;
+} gf_stats;
+
+/* Host landing pad for a user opcode (>= 256).  `rec` points at the lane
+ * record (layout in gf_layout.h: gf_rec_hdr, tags, words, tail); the return
+ * value is handed back to the calling lane.  Write-mode reference arguments
+ * may be modified in place in the record's tail; they are copied back. */
+typedef int64_t (*gf_host_fn)(void *user, uint32_t opcode, void *rec);
+
+typedef struct gf_serve_opts {
+    int64_t timeout_ns;           /* return GF_ETIMEDOUT after this long (<= 0: no limit)   */
+    volatile int32_t *stop;       /* return GF_OK when *stop becomes nonzero (may be NULL)  */
+} gf_serve_opts;
+
+/* ------------------------------------------------------------------ lifecycle */
+
+/* Fill *cfg with the defaults listed in gf_config. */
+GF_API void gf_config_default(gf_config *cfg);
+
+/* Create a context on the configured device: device heap arenas, the pinned
+ * and device-mapped RPC ring, per-instance program state, DMA staging and the
+ * host server threads.  cfg may be NULL (defaults).  *out receives the
+ * context.  Errors: GF_EINVAL (bad sizes), GF_ENOMEM, GF_ECUDA. */
+GF_API int gf_init(const gf_config *cfg, gf_ctx **out);
+
+/* Stop the server threads, close files the programs left open, free all
+ * context memory.  Programs still running are waited for first.  NULL is a
+ * no-op returning GF_OK. */
+GF_API int gf_finalize(gf_ctx *ctx);
+
+/* Registry id of the program registered as GF_MAIN(name).  GF_ENOENT if none. */
+GF_API int gf_program_lookup(gf_ctx *ctx, const char *name, gf_program *out);
+
+/* ------------------------------------------------------------------ running programs */
+
+/* The loader (paper Sec. 3.1: map argv to the device, start the RPC server,
+ * call main on the GPU): copy argv (and host buffers marked GF_BUF_IN) to the
+ * device, launch the program's persistent cooperative grid on cfg.stream,
+ * serve its RPCs until main returns, copy GF_BUF_OUT host buffers back and
+ * store main's return value in *exit_code.  Blocking.  argv strings are copied
+ * (at most 64 KiB in total); bufs may be NULL when nbufs is 0 (at most 16).
+ * Returns GF_OK, or the first device error (GF_ETIMEDOUT, GF_ERING, ...),
+ * GF_EBUSY when every instance is taken, GF_ECUDA on a launch failure. */
+GF_API int gf_run_main(gf_ctx *ctx, gf_program prog, int argc, const char *const *argv,
+                       const gf_buf *bufs, int nbufs, int *exit_code);
+
+/* Asynchronous launch for serving and batching: like gf_run_main up to the
+ * kernel launch, on `stream` (NULL = cfg.stream) with `grid` blocks (0 = the
+ * configured share).  *h receives the handle.  GF_EBUSY when no instance is
+ * free (admission by ring and heap capacity). */
+GF_API int gf_launch(gf_ctx *ctx, gf_program prog, int argc, const char *const *argv,
+                     const gf_buf *bufs, int nbufs, void *stream, uint32_t grid, gf_handle **h);
+
+/* 1 if the program behind h has finished (its kernel completed), else 0. */
+GF_API int gf_done(gf_handle *h);
+
+/* Wait for the program behind h (serving its RPCs when the context has no
+ * server threads), copy back GF_BUF_OUT host buffers, release the instance and
+ * free h.  timeout_ns <= 0 waits without limit; on GF_ETIMEDOUT h stays valid. */
+GF_API int gf_wait(gf_handle *h, int *exit_code, int64_t timeout_ns);
+
+/* Serve RPCs of all running programs in the calling thread until none is
+ * running, *opts->stop becomes nonzero, or the timeout passes. */
+GF_API int gf_rpc_serve(gf_ctx *ctx, const gf_serve_opts *opts);
+
+/* Register a host landing pad for opcode >= 256 (device: gf_rpc(opcode, ...)). */
+GF_API int gf_rpc_register(gf_ctx *ctx, uint32_t opcode, gf_host_fn fn, void *user);
+
+/* Counters of the last program waited for (see gf_stats). */
+GF_API int gf_get_stats(gf_ctx *ctx, gf_stats *out);
+
+/* Static message for an error code. */
+GF_API const char *gf_strerror(int err);
+
+/* Number of SMs and resident blocks per SM that a program's grid uses at
+ * `block` threads (for sizing, tests and roofline accounting). */
+GF_API int gf_grid_info(gf_ctx *ctx, gf_program prog, uint32_t *sms, uint32_t *blocks_per_sm);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,433 @@
+/*
+ * Device side of host RPC (paper Sec. 3.2, Fig. 4 and Sec. 5.2).
+ *
+ * A call site packs its arguments into a lane record: value arguments
+ * (integers, doubles, opaque handles such as FILE*) as tagged 8-byte words,
+ * reference arguments (strings, small objects with a read / write / readwrite
+ * mode) as bytes in the record's tail, large objects as a device address that
+ * the host moves by DMA.  The opcode names the host landing pad.
+ *
+ * Warp aggregation: the lanes of a warp that call the same opcode with the
+ * same format and argument signature are grouped with __match_any_sync; their
+ * leader claims ONE ring slot, every lane writes its record at its rank's
+ * offset, the leader publishes the slot with a system-scope release store,
+ * waits (bounded) for the host's release of the returns, and each lane reads
+ * its own return value.  With aggregation off every lane takes its own slot,
+ * which is the per-thread RPC of the paper.
+ *
+ * Format strings are shipped inside the slot the first time and cached on the
+ * host by device address afterwards (the paper copies them on every call).
+ * A format string must therefore not change while the context lives (string
+ * literals are the intended use).
+ */
+#ifndef GF_DEVICE_RPC_CUH
+#define GF_DEVICE_RPC_CUH
+
+#define GF_INLINE_BLOB_MAX 2048u    /* larger objects move by DMA */
+
+namespace gfd {
+
+struct argpack {
+    uint32_t n, tail;
+    char tag[GF_MAX_ARGS];
+    uint64_t word[GF_MAX_ARGS];
+    const void *src[GF_MAX_ARGS];
+    uint32_t len[GF_MAX_ARGS];
+    __device__ argpack() : n(0), tail(0) {}
+    __device__ void val(char t, uint64_t w)
+    {
+        if (n < GF_MAX_ARGS) {
+            tag[n] = t;
+            word[n] = w;
+            src[n] = nullptr;
+            len[n] = 0;
+            n++;
+        }
+    }
+    __device__ void blob(char t, const void *p, uint32_t bytes)
+    {
+        if (n < GF_MAX_ARGS) {
+            tag[n] = t;
+            word[n] = ((uint64_t)bytes << 32) | tail;   /* offset in tail | bytes */
+            src[n] = p;
+            len[n] = bytes;
+            tail += (bytes + 7u) & ~7u;
+            n++;
+        }
+    }
+    __device__ uint32_t bytes() const { return 16u + ((n + 7u) & ~7u) + 8u * n + tail; }
+    __device__ uint64_t signature(uint32_t op, uint64_t key) const
+    {
+        uint64_t h = 0xcbf29ce484222325ull ^ ((uint64_t)op << 48) ^ key;
+        for (uint32_t k = 0; k < n; k++)
+            h = (h ^ (uint8_t)tag[k]) * 0x100000001b3ull;
+        return h;
+    }
+};
+
+/* reference-argument wrappers (paper Fig. 4: addRefArg(ptr, mode, size, offset)) */
+struct ref_r { const void *p; uint32_t bytes; };
+struct ref_w { void *p; uint32_t bytes; };
+struct ref_rw { void *p; uint32_t bytes; };
+struct dma_ref { uint64_t addr; uint64_t bytes; };
+
+__device__ inline void pack1(argpack &a, int v) { a.val(GF_T_I32, (uint64_t)(int64_t)v); }
+__device__ inline void pack1(argpack &a, unsigned v) { a.val(GF_T_U32, (uint64_t)v); }
+__device__ inline void pack1(argpack &a, long v) { a.val(GF_T_I64, (uint64_t)v); }
+__device__ inline void pack1(argpack &a, long long v) { a.val(GF_T_I64, (uint64_t)v); }
+__device__ inline void pack1(argpack &a, unsigned long v) { a.val(GF_T_U64, (uint64_t)v); }
+__device__ inline void pack1(argpack &a, unsigned long long v) { a.val(GF_T_U64, (uint64_t)v); }
+__device__ inline void pack1(argpack &a, double v) { a.val(GF_T_F64, (uint64_t)__double_as_longlong(v)); }
+__device__ inline void pack1(argpack &a, float v) { pack1(a, (double)v); }
+__device__ inline void pack1(argpack &a, char v) { pack1(a, (int)v); }
+__device__ inline void pack1(argpack &a, short v) { pack1(a, (int)v); }
+__device__ inline void pack1(argpack &a, bool v) { pack1(a, (int)v); }
+__device__ inline void pack1(argpack &a, const char *s)
+{
+    if (!s) { a.val(GF_T_PTR, 0); return; }
+    a.blob(GF_T_STR, s, gf_strlen(s) + 1u);
+}
+__device__ inline void pack1(argpack &a, char *s) { pack1(a, (const char *)s); }
+__device__ inline void pack1(argpack &a, const void *p) { a.val(GF_T_PTR, (uint64_t)p); }
+__device__ inline void pack1(argpack &a, void *p) { a.val(GF_T_PTR, (uint64_t)p); }
+__device__ inline void pack1(argpack &a, ref_r r) { a.blob(GF_T_BLOB_R, r.p, r.bytes); }
+__device__ inline void pack1(argpack &a, ref_w r) { a.blob(GF_T_BLOB_W, r.p, r.bytes); }
+__device__ inline void pack1(argpack &a, ref_rw r) { a.blob(GF_T_BLOB_RW, r.p, r.bytes); }
+__device__ inline void pack1(argpack &a, dma_ref r)
+{
+    a.val(GF_T_DMA, r.addr);
+    a.val(GF_T_U64, r.bytes);
+}
+__device__ inline void pack_all(argpack &) {}
+template <class A0, class... A> __device__ inline void pack_all(argpack &a, A0 a0, A... rest)
+{
+    pack1(a, a0);
+    pack_all(a, rest...);
+}
+
+/* copy `bytes` from any device-readable address into 8-byte-aligned mapped memory */
+__device__ inline void copy_out(uint64_t *dst, const void *src, uint32_t bytes)
+{
+    const uint32_t nw = (bytes + 7u) >> 3;
+    if (((uintptr_t)src & 7u) == 0) {
+        const uint64_t *s = (const uint64_t *)src;
+        for (uint32_t k = 0; k + 1 < nw || (k < nw && (bytes & 7u) == 0); k++)
+            dst[k] = s[k];
+        if (bytes & 7u) {
+            const uint8_t *b = (const uint8_t *)src + 8u * (nw - 1);
+            uint64_t w = 0;
+            for (uint32_t j = 0; j < (bytes & 7u); j++)
+                w |= (uint64_t)b[j] << (8 * j);
+            dst[nw - 1] = w;
+        }
+    } else {
+        const uint8_t *b = (const uint8_t *)src;
+        for (uint32_t k = 0; k < nw; k++) {
+            uint64_t w = 0;
+            for (uint32_t j = 0; j < 8 && 8 * k + j < bytes; j++)
+                w |= (uint64_t)b[8 * k + j] << (8 * j);
+            dst[k] = w;
+        }
+    }
+}
+
+__device__ inline void copy_back(void *dst, const uint64_t *src, uint32_t bytes)
+{
+    uint8_t *d = (uint8_t *)dst;
+    for (uint32_t k = 0; k < bytes; k += 8) {
+        uint64_t w = ld_vol64(src + k / 8);
+        for (uint32_t j = 0; j < 8 && k + j < bytes; j++)
+            d[k + j] = (uint8_t)(w >> (8 * j));
+    }
+}
+
+__device__ inline void write_rec(uint8_t *dst, const argpack &a, uint32_t lane, uint32_t gtid)
+{
+    uint64_t *w = (uint64_t *)dst;
+    const uint32_t bytes = a.bytes();
+    w[0] = (uint64_t)bytes | ((uint64_t)a.n << 32) | ((uint64_t)lane << 48);
+    w[1] = (uint64_t)gtid;
+    uint32_t k = 2;
+    for (uint32_t t = 0; t < a.n; t += 8) {
+        uint64_t tw = 0;
+        for (uint32_t j = 0; j < 8 && t + j < a.n; j++)
+            tw |= (uint64_t)(uint8_t)a.tag[t + j] << (8 * j);
+        w[k++] = tw;
+    }
+    for (uint32_t t = 0; t < a.n; t++)
+        w[k++] = a.word[t];
+    for (uint32_t t = 0; t < a.n; t++)
+        if (a.src[t] && a.tag[t] != GF_T_BLOB_W)
+            copy_out(w + k + (uint32_t)(a.word[t] & 0xffffffffu) / 8, a.src[t], a.len[t]);
+}
+
+/* fmt cache: open addressing over device-address keys of shipped formats */
+__device__ inline bool fmt_known(gf_state *S, uint64_t key)
+{
+    if (!key || !S->fmt_cache_cap)
+        return false;
+    const unsigned long long *tab = (const unsigned long long *)S->fmt_cache;
+    uint32_t m = S->fmt_cache_cap - 1, h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & m;
+    for (uint32_t p = 0; p < 16; p++) {
+        unsigned long long v = *(volatile const unsigned long long *)&tab[(h + p) & m];
+        if (v == key)
+            return true;
+        if (v == 0)
+            return false;
+    }
+    return false;
+}
+__device__ inline void fmt_insert(gf_state *S, uint64_t key)
+{
+    if (!key || !S->fmt_cache_cap)
+        return;
+    unsigned long long *tab = (unsigned long long *)S->fmt_cache;
+    uint32_t m = S->fmt_cache_cap - 1, h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & m;
+    for (uint32_t p = 0; p < 16; p++) {
+        unsigned long long old = atomicCAS(&tab[(h + p) & m], 0ull, (unsigned long long)key);
+        if (old == 0 || old == key)
+            return;
+    }
+}
+
+/*
+ * Issue one RPC from every calling lane; returns this lane's host result.
+ * *status receives GF_OK, GF_ERING (no slot credit within the timeout),
+ * GF_ETIMEDOUT (host did not answer) or GF_EINVAL (record larger than a slot).
+ */
+static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, const argpack &a, int *status)
+{
+    gf_state *S = s_st;
+    const uint32_t lane = lane_id();
+    const uint32_t active = __activemask();
+    const uint64_t key = (uint64_t)fmt;
+    const uint64_t sig = a.signature(op, key);
+    const uint32_t grp = S->aggregate ? __match_any_sync(active, sig) : (1u << lane);
+    const uint32_t my = a.bytes();
+    const uint32_t gtid = is_initial_thread() ? 0xffffffffu : (uint32_t)gf_thread_num();
+    const uint32_t fmt_len = fmt ? gf_strlen(fmt) + 1u : 0u;
+    const uint32_t slot_cap = S->slot_bytes - GF_SLOT_PAYLOAD_OFF;
+
+    uint32_t remaining = grp;
+    int64_t ret = -1;
+    int st = GF_OK;
+    while (remaining) {
+        const bool in_round = (remaining >> lane) & 1u;
+        /* format shipping is decided once per round by its leader */
+        const uint32_t rl = __ffs(remaining) - 1;
+        int ship = 0;
+        if (lane == rl)
+            ship = (fmt && !fmt_known(S, key)) ? 1 : 0;
+        ship = __shfl_sync(grp, ship, rl);
+        const uint32_t fbytes = ship ? ((fmt_len + 7u) & ~7u) : 0u;
+        const uint32_t cap = slot_cap > fbytes ? slot_cap - fbytes : 0u;
+        /* exclusive prefix of record sizes over the lanes still waiting */
+        const uint32_t v = in_round ? my : 0u;
+        uint32_t off = 0;
+        int same = 0;
+        __match_all_sync(grp, v, &same);
+        if (same) {
+            off = v * __popc(remaining & lanemask_lt());
+        } else {
+            for (uint32_t m = grp; m; m &= m - 1) {
+                const uint32_t l = __ffs(m) - 1;
+                const uint32_t x = __shfl_sync(grp, v, l);
+                if (l < lane)
+                    off += x;
+            }
+        }
+        uint32_t take = __ballot_sync(grp, in_round && off + my <= cap);
+        bool oversized = false;
+        if (!take) {               /* a single record larger than a slot: reject that lane */
+            take = 1u << rl;
+            oversized = true;
+        }
+        remaining &= ~take;
+        const bool mine = (take >> lane) & 1u;
+        if (oversized) {
+            if (mine) {
+                st = GF_EINVAL;
+                ret = -1;
+            }
+            continue;
+        }
+        const uint32_t leader = __ffs(take) - 1;
+        const uint32_t rank = __popc(take & lanemask_lt());
+        const uint32_t nl = __popc(take);
+        /* leader claims a ticket and waits for the slot's credit */
+        unsigned long long t = 0;
+        int cst = GF_OK;
+        uint64_t t_issue = 0;
+        if (lane == leader) {
+            t_issue = now_ns();
+            t = atomicAdd(&S->rpc_ticket, 1ull);
+            uint64_t *seq = (uint64_t *)(S->ring_slots + (t % S->nslots) * (uint64_t)S->slot_bytes);
+            backoff bo(S->timeout_ns);
+            while (ld_acq_sys64(seq) != t)
+                if (!bo.wait()) {
+                    cst = GF_ERING;
+                    break;
+                }
+        }
+        t = __shfl_sync(grp, t, leader);
+        cst = __shfl_sync(grp, cst, leader);
+        if (cst != GF_OK) {
+            if (mine) {
+                st = cst;
+                ret = -1;
+            }
+            if (lane == leader)
+                set_error(cst);
+            continue;
+        }
+        uint8_t *slot = (uint8_t *)(S->ring_slots + (t % S->nslots) * (uint64_t)S->slot_bytes);
+        gf_slot_hdr *h = (gf_slot_hdr *)slot;
+        uint8_t *payload = slot + GF_SLOT_PAYLOAD_OFF;
+        if (mine)
+            write_rec(payload + fbytes + off, a, lane, gtid);
+        if (lane == leader) {
+            if (ship)
+                copy_out((uint64_t *)payload, fmt, fmt_len);
+            h->opcode = op;
+            h->nlanes = nl;
+            h->flags = ship ? GF_SF_FMT_INLINE : 0u;
+            h->fmt_len = ship ? fmt_len : 0u;
+            h->fmt_key = key;
+            h->prog = S->prog_id;
+            h->t_issue = t_issue;
+        }
+        __threadfence_system();
+        __syncwarp(grp);
+        int wst = GF_OK;
+        if (lane == leader) {
+            h->payload_bytes = 0;   /* the host walks records by their own sizes */
+            h->t_publish = now_ns();
+            st_rel_sys64(&h->seq, t + 1);
+            backoff bo(S->timeout_ns);
+            const uint64_t t0 = now_ns();
+            while (ld_acq_sys64(&h->seq) != t + 2)
+                if (!bo.wait()) {
+                    wst = GF_ETIMEDOUT;
+                    break;
+                }
+            atomicAdd((unsigned long long *)&S->st_wait_ns, (unsigned long long)(now_ns() - t0));
+            if (wst == GF_OK) {
+                const uint64_t lat = now_ns() - t_issue;
+                uint32_t bk = (uint32_t)lat;
+                if (lat >= 8) {
+                    const uint32_t e = 63 - __clzll((long long)lat);
+                    bk = 8u * e + (uint32_t)((lat >> (e - 3)) & 7u);
+                }
+                if (bk >= GF_LAT_BUCKETS)
+                    bk = GF_LAT_BUCKETS - 1;
+                atomicAdd((unsigned long long *)&S->lat_hist[bk], (unsigned long long)nl);
+                atomicAdd((unsigned long long *)&S->st_calls[op < GF_NSTAT ? op : 0], (unsigned long long)nl);
+                atomicAdd((unsigned long long *)&S->st_slots[op < GF_NSTAT ? op : 0], 1ull);
+            } else {
+                set_error(wst);
+            }
+        }
+        wst = __shfl_sync(grp, wst, leader);
+        if (wst == GF_OK && mine) {
+            ret = (int64_t)ld_vol64((const uint64_t *)(slot + GF_SLOT_RET_OFF) + rank);
+            /* copy back written reference arguments (mode write / readwrite) */
+            const uint64_t *rw = (const uint64_t *)(payload + fbytes + off);
+            const uint32_t ntag = (a.n + 7u) & ~7u;
+            const uint64_t *tail = rw + 2 + ntag / 8 + a.n;
+            for (uint32_t k = 0; k < a.n; k++)
+                if (a.tag[k] == GF_T_BLOB_W || a.tag[k] == GF_T_BLOB_RW)
+                    copy_back((void *)a.src[k], tail + (uint32_t)(a.word[k] & 0xffffffffu) / 8, a.len[k]);
+        } else if (mine) {
+            st = wst;
+            ret = -1;
+        }
+        __syncwarp(grp);
+        if (lane == leader && wst == GF_OK) {
+            if (ship)
+                fmt_insert(S, key);
+            st_rel_sys64(&h->seq, t + S->nslots);
+        }
+    }
+    if (status)
+        *status = st;
+    return ret;
+}
+
+template <class... A> __device__ inline int64_t rpc(uint32_t op, const char *fmt, int *status, A... args)
+{
+    argpack a;
+    pack_all(a, args...);
+    return rpc_issue(op, fmt, a, status);
+}
+
+} // namespace gfd
+
+/* ====================================================================== libc over RPC */
+/* printf family: formatted on the host by the real libc, one landing pad per
+ * argument-type signature (paper Fig. 4b), records grouped per warp. */
+template <class... A> __device__ inline int gf_printf(const char *fmt, A... args)
+{
+    return (int)gfd::rpc(GF_OP_PRINTF, fmt, nullptr, (unsigned long long)GF_STDOUT_H, args...);
+}
+template <class... A> __device__ inline int gf_fprintf(GF_FILE f, const char *fmt, A... args)
+{
+    return (int)gfd::rpc(GF_OP_PRINTF, fmt, nullptr, (unsigned long long)f, args...);
+}
+__device__ inline GF_FILE gf_stdout() { return GF_STDOUT_H; }
+__device__ inline GF_FILE gf_stderr() { return GF_STDERR_H; }
+
+__device__ inline GF_FILE gf_fopen(const char *path, const char *mode)
+{
+    return (GF_FILE)gfd::rpc(GF_OP_FOPEN, nullptr, nullptr, path, mode);
+}
+__device__ inline int gf_fclose(GF_FILE f)
+{
+    return (int)gfd::rpc(GF_OP_FCLOSE, nullptr, nullptr, (unsigned long long)f);
+}
+__device__ inline int gf_fflush(GF_FILE f)
+{
+    return (int)gfd::rpc(GF_OP_FFLUSH, nullptr, nullptr, (unsigned long long)f);
+}
+/* fwrite: small objects travel inside the slot, large ones are read by the
+ * host with a copy-engine DMA straight from device memory. */
+__device__ inline size_t gf_fwrite(const void *buf, size_t size, size_t n, GF_FILE f)
+{
+    const uint64_t bytes = (uint64_t)size * n;
+    __threadfence_system();
+    if (bytes <= GF_INLINE_BLOB_MAX)
+        return (size_t)gfd::rpc(GF_OP_FWRITE, nullptr, nullptr, (unsigned long long)size,
+                                (unsigned long long)n, (unsigned long long)f, gfd::ref_r{buf, (uint32_t)bytes});
+    return (size_t)gfd::rpc(GF_OP_FWRITE, nullptr, nullptr, (unsigned long long)size, (unsigned long long)n,
+                            (unsigned long long)f, gfd::dma_ref{(uint64_t)buf, bytes});
+}
+__device__ inline size_t gf_fread(void *buf, size_t size, size_t n, GF_FILE f)
+{
+    const uint64_t bytes = (uint64_t)size * n;
+    if (bytes <= GF_INLINE_BLOB_MAX)
+        return (size_t)gfd::rpc(GF_OP_FREAD, nullptr, nullptr, (unsigned long long)size,
+                                (unsigned long long)n, (unsigned long long)f, gfd::ref_w{buf, (uint32_t)bytes});
+    size_t r = (size_t)gfd::rpc(GF_OP_FREAD, nullptr, nullptr, (unsigned long long)size, (unsigned long long)n,
+                                (unsigned long long)f, gfd::dma_ref{(uint64_t)buf, bytes});
+    __threadfence();
+    return r;
+}
+__device__ inline long long gf_clock()
+{
+    return (long long)gfd::rpc(GF_OP_CLOCK, nullptr, nullptr);
+}
+/* getenv: the host interns the value in device-readable mapped memory that
+ * lives as long as the context; NULL when unset. */
+__device__ inline const char *gf_getenv(const char *name)
+{
+    return (const char *)gfd::rpc(GF_OP_GETENV, nullptr, nullptr, name);
+}
+/* generic RPC to a landing pad registered with gf_rpc_register */
+template <class... A> __device__ inline int64_t gf_rpc(uint32_t opcode, int *status, A... args)
+{
+    return gfd::rpc(opcode, nullptr, status, args...);
+}
+__device__ inline gfd::ref_r gf_ref_read(const void *p, uint32_t bytes) { return gfd::ref_r{p, bytes}; }
+__device__ inline gfd::ref_w gf_ref_write(void *p, uint32_t bytes) { return gfd::ref_w{p, bytes}; }
+__device__ inline gfd::ref_rw gf_ref_readwrite(void *p, uint32_t bytes) { return gfd::ref_rw{p, bytes}; }
+
+#endif

@@ -1,0 +1,475 @@
+/* Host RPC server: slot scanning and the libc landing pads (see server.h). */
+#include "server.h"
+
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+#include <chrono>
+#include <vector>
+
+namespace gfh {
+
+static inline uint64_t acquire_load(const uint64_t *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+static inline void release_store(uint64_t *p, uint64_t v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
+static inline uint64_t now_ns()
+{
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+void Segment::reset(uint32_t nthreads)
+{
+    head.assign(nthreads, 0);
+    for (uint32_t t = 0; t < nthreads; t++)
+        head[t] = t;                    /* thread t serves tickets t, t + nthreads, ... */
+    served.assign(nslots, 0);
+    std::lock_guard<std::mutex> g(fmt_mu);
+    fmt_cache.clear();
+}
+
+RecView::RecView(const uint8_t *r) : base(r)
+{
+    const gf_rec_hdr *h = (const gf_rec_hdr *)r;
+    bytes = h->bytes;
+    nargs = h->nargs;
+    tags = r + sizeof(gf_rec_hdr);
+    words = (const uint64_t *)(tags + ((nargs + 7u) & ~7u));
+    tail = (const uint8_t *)(words + nargs);
+}
+
+Server::Server() {}
+Server::~Server() { close_all(); }
+
+void Server::set_stdout(FILE *f) { out_ = f ? f : stdout; }
+void Server::set_dma(d2h_fn d2h, h2d_fn h2d)
+{
+    d2h_ = d2h;
+    h2d_ = h2d;
+}
+int Server::register_user(uint32_t opcode, user_fn fn, void *user)
+{
+    std::lock_guard<std::mutex> g(user_mu_);
+    user_[opcode] = {fn, user};
+    return 0;
+}
+
+void Server::close_all()
+{
+    std::lock_guard<std::mutex> g(files_mu_);
+    for (uint64_t h : files_)
+        fclose((FILE *)(uintptr_t)h);
+    files_.clear();
+    std::lock_guard<std::mutex> g2(out_mu_);
+    fflush(out_);
+}
+
+FILE *Server::file_of(uint64_t h)
+{
+    if (h == GF_STDOUT_H)
+        return out_;
+    if (h == GF_STDERR_H)
+        return stderr;
+    std::lock_guard<std::mutex> g(files_mu_);
+    return files_.count(h) ? (FILE *)(uintptr_t)h : nullptr;
+}
+
+void Server::emit(uint64_t stream, const std::string &s)
+{
+    if (s.empty())
+        return;
+    FILE *f = file_of(stream);
+    if (!f)
+        return;
+    std::lock_guard<std::mutex> g(out_mu_);
+    fwrite(s.data(), 1, s.size(), f);
+}
+
+/*
+ * printf landing pad: walk the format, and for each conversion call snprintf
+ * with exactly that conversion and an argument of the C type it names.  The
+ * output equals one printf call with the same arguments, because printf's
+ * output is the concatenation of its literal text and its conversions.
+ */
+int64_t Server::do_printf(const char *fmt, const uint8_t *recp, std::string &out, uint64_t *stream)
+{
+    RecView r(recp);
+    if (r.nargs < 1 || !fmt)
+        return -1;
+    *stream = r.word(0);
+    uint32_t ai = 1;
+    const size_t start = out.size();
+    char spec[64], buf[512];
+    for (const char *p = fmt; *p;) {
+        if (*p != '%') {
+            const char *q = strchr(p, '%');
+            size_t n = q ? (size_t)(q - p) : strlen(p);
+            out.append(p, n);
+            p += n;
+            continue;
+        }
+        if (p[1] == '%') {
+            out.push_back('%');
+            p += 2;
+            continue;
+        }
+        /* %[flags][width][.prec][length]conv */
+        const char *s0 = p++;
+        while (*p && strchr("-+ #0'", *p))
+            p++;
+        int star_w = 0, star_p = 0;
+        if (*p == '*') {
+            star_w = 1;
+            p++;
+        } else
+            while (*p >= '0' && *p <= '9')
+                p++;
+        if (*p == '.') {
+            p++;
+            if (*p == '*') {
+                star_p = 1;
+                p++;
+            } else
+                while (*p >= '0' && *p <= '9')
+                    p++;
+        }
+        char len[3] = {0, 0, 0};
+        if (*p == 'h' || *p == 'l') {
+            len[0] = *p++;
+            if (*p == len[0])
+                len[1] = *p++;
+        } else if (*p == 'j' || *p == 'z' || *p == 't' || *p == 'L' || *p == 'q') {
+            len[0] = *p++;
+        }
+        const char conv = *p;
+        if (!conv)
+            break;
+        p++;
+        size_t sl = (size_t)(p - s0);
+        if (sl >= sizeof(spec))
+            return -1;
+        memcpy(spec, s0, sl);
+        spec[sl] = 0;
+        int wv = 0, pv = 0;
+        if (star_w) {
+            if (ai >= r.nargs)
+                break;
+            wv = (int)(int64_t)r.word(ai++);
+        }
+        if (star_p) {
+            if (ai >= r.nargs)
+                break;
+            pv = (int)(int64_t)r.word(ai++);
+        }
+        if (conv == 'n') {           /* no host-side write-back of %n */
+            if (ai < r.nargs)
+                ai++;
+            continue;
+        }
+        if (ai >= r.nargs)
+            break;
+        const uint32_t k = ai++;
+        const uint64_t w = r.word(k);
+        int n = 0;
+        char *dst = buf;
+        std::string big;
+#define GF_FMT(VAL)                                                                                 \
+    do {                                                                                            \
+        if (star_w && star_p)                                                                       \
+            n = snprintf(dst, sizeof(buf), spec, wv, pv, VAL);                                      \
+        else if (star_w || star_p)                                                                  \
+            n = snprintf(dst, sizeof(buf), spec, star_w ? wv : pv, VAL);                            \
+        else                                                                                        \
+            n = snprintf(dst, sizeof(buf), spec, VAL);                                              \
+        if (n >= (int)sizeof(buf)) {                                                                \
+            big.resize((size_t)n + 1);                                                              \
+            if (star_w && star_p)                                                                   \
+                snprintf(&big[0], big.size(), spec, wv, pv, VAL);                                   \
+            else if (star_w || star_p)                                                              \
+                snprintf(&big[0], big.size(), spec, star_w ? wv : pv, VAL);                         \
+            else                                                                                    \
+                snprintf(&big[0], big.size(), spec, VAL);                                           \
+            dst = &big[0];                                                                          \
+        }                                                                                           \
+    } while (0)
+        switch (conv) {
+        case 'd':
+        case 'i':
+            if (len[0] == 'l' && len[1] == 'l')
+                GF_FMT((long long)w);
+            else if (len[0] == 'l' || len[0] == 'j' || len[0] == 'z' || len[0] == 't' || len[0] == 'q')
+                GF_FMT((long)w);
+            else if (len[0] == 'h' && len[1] == 'h')
+                GF_FMT((int)(signed char)w);
+            else if (len[0] == 'h')
+                GF_FMT((int)(short)w);
+            else
+                GF_FMT((int)w);
+            break;
+        case 'u':
+        case 'o':
+        case 'x':
+        case 'X':
+            if (len[0] == 'l' && len[1] == 'l')
+                GF_FMT((unsigned long long)w);
+            else if (len[0] == 'l' || len[0] == 'j' || len[0] == 'z' || len[0] == 't' || len[0] == 'q')
+                GF_FMT((unsigned long)w);
+            else if (len[0] == 'h' && len[1] == 'h')
+                GF_FMT((unsigned)(unsigned char)w);
+            else if (len[0] == 'h')
+                GF_FMT((unsigned)(unsigned short)w);
+            else
+                GF_FMT((unsigned)w);
+            break;
+        case 'c':
+            GF_FMT((int)w);
+            break;
+        case 'e':
+        case 'E':
+        case 'f':
+        case 'F':
+        case 'g':
+        case 'G':
+        case 'a':
+        case 'A': {
+            double d;
+            memcpy(&d, &w, 8);
+            if (r.tag(k) != GF_T_F64) /* an integer passed to a float conversion */
+                d = (double)(int64_t)w;
+            if (len[0] == 'L')
+                GF_FMT((long double)d);
+            else
+                GF_FMT(d);
+            break;
+        }
+        case 's': {
+            const char *sv = r.tag(k) == GF_T_STR ? r.str(k) : (w == 0 ? "(null)" : "(?)");
+            GF_FMT(sv);
+            break;
+        }
+        case 'p':
+            GF_FMT((void *)(uintptr_t)w);
+            break;
+        default:
+            out.append(spec);
+            continue;
+        }
+#undef GF_FMT
+        if (n > 0)
+            out.append(dst, (size_t)n);
+    }
+    return (int64_t)(out.size() - start);
+}
+
+int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec)
+{
+    RecView r(rec);
+    switch (op) {
+    case GF_OP_PRINTF: {
+        std::string s;
+        uint64_t stream = 0;
+        int64_t n = do_printf(fmt, rec, s, &stream);
+        if (n >= 0) {
+            if (!file_of(stream))
+                return -1;
+            emit(stream, s);
+        }
+        return n;
+    }
+    case GF_OP_FOPEN: {
+        if (r.nargs < 2 || r.tag(0) != GF_T_STR || r.tag(1) != GF_T_STR)
+            return 0;
+        FILE *f = fopen(r.str(0), r.str(1));
+        if (!f)
+            return 0;
+        std::lock_guard<std::mutex> g(files_mu_);
+        files_.insert((uint64_t)(uintptr_t)f);
+        return (int64_t)(uintptr_t)f;
+    }
+    case GF_OP_FCLOSE: {
+        if (r.nargs < 1)
+            return -1;
+        const uint64_t h = r.word(0);
+        std::lock_guard<std::mutex> g(files_mu_);
+        if (!files_.count(h))
+            return -1;
+        files_.erase(h);
+        return fclose((FILE *)(uintptr_t)h);
+    }
+    case GF_OP_FFLUSH: {
+        if (r.nargs < 1)
+            return -1;
+        FILE *f = file_of(r.word(0));
+        if (!f)
+            return -1;
+        std::lock_guard<std::mutex> g(out_mu_);
+        return fflush(f);
+    }
+    case GF_OP_FWRITE:
+    case GF_OP_FREAD: {
+        /* (size, nmemb, FILE*, blob | DMA addr + bytes) */
+        if (r.nargs < 4)
+            return 0;
+        const uint64_t size = r.word(0), nmemb = r.word(1);
+        FILE *f = file_of(r.word(2));
+        if (!f || size == 0)
+            return 0;
+        const uint64_t bytes = size * nmemb;
+        if (r.tag(3) != GF_T_DMA) {
+            uint8_t *b = r.blob(3);
+            if (r.blob_len(3) < bytes)
+                return 0;
+            std::lock_guard<std::mutex> g(out_mu_);
+            return op == GF_OP_FWRITE ? (int64_t)fwrite(b, size, nmemb, f) : (int64_t)fread(b, size, nmemb, f);
+        }
+        const uint64_t dev = r.word(3);
+        uint64_t done = 0;
+        std::lock_guard<std::mutex> g(out_mu_);
+        if (op == GF_OP_FWRITE) {
+            if (!d2h_)
+                return 0;
+            done = d2h_(dev, bytes, [&](const void *c, uint64_t n) { return fwrite(c, 1, n, f) == n; });
+        } else {
+            if (!h2d_)
+                return 0;
+            done = h2d_(dev, bytes, [&](void *c, uint64_t want) { return (uint64_t)fread(c, 1, want, f); });
+        }
+        stats.dma_bytes += done;
+        return (int64_t)(done / size);
+    }
+    case GF_OP_CLOCK:
+        return (int64_t)clock();
+    case GF_OP_GETENV: {
+        if (r.nargs < 1 || r.tag(0) != GF_T_STR || !intern_)
+            return 0;
+        std::string name = r.str(0);
+        std::lock_guard<std::mutex> g(intern_mu_);
+        auto it = interned_.find(name);
+        if (it != interned_.end())
+            return (int64_t)it->second;
+        const char *v = getenv(name.c_str());
+        uint64_t a = v ? intern_(std::string(v)) : 0;
+        interned_[name] = a;
+        return (int64_t)a;
+    }
+    default: {
+        std::pair<user_fn, void *> u{nullptr, nullptr};
+        {
+            std::lock_guard<std::mutex> g(user_mu_);
+            auto it = user_.find(op);
+            if (it != user_.end())
+                u = it->second;
+        }
+        if (!u.first)
+            return -1;
+        return u.first(u.second, op, (void *)rec);
+    }
+    }
+}
+
+int Server::poll(Segment &seg, uint32_t tid, uint32_t nthr)
+{
+    if (!seg.active.load(std::memory_order_acquire))
+        return 0;
+    const uint32_t N = seg.nslots;
+    int served = 0;
+    uint64_t t = seg.head[tid];
+    uint32_t gap = 0;
+    /* scan from the lowest unserved ticket; stop after a run of unpublished slots */
+    for (uint64_t scanned = 0; scanned < N && gap < 64; scanned += nthr, t += nthr) {
+        const uint32_t s = (uint32_t)(t % N);
+        uint8_t *slot = seg.slots + (uint64_t)s * seg.slot_bytes;
+        gf_slot_hdr *h = (gf_slot_hdr *)slot;
+        if (seg.served[s] == t + 1) {          /* already served, device not yet done with it */
+            gap = 0;
+            continue;
+        }
+        const uint64_t q = acquire_load(&h->seq);
+        if (q != t + 1) {
+            gap++;
+            continue;
+        }
+        gap = 0;
+        const uint64_t t0 = now_ns();
+        const uint32_t op = h->opcode, nl = h->nlanes;
+        uint8_t *pay = slot + GF_SLOT_PAYLOAD_OFF;
+        const char *fmt = nullptr;
+        std::string fmt_s;
+        if (h->flags & GF_SF_FMT_INLINE) {
+            fmt = (const char *)pay;
+            fmt_s.assign(fmt, strnlen(fmt, h->fmt_len));
+            {
+                std::lock_guard<std::mutex> g(seg.fmt_mu);
+                seg.fmt_cache[h->fmt_key] = fmt_s;
+            }
+            pay += (h->fmt_len + 7u) & ~7u;
+        } else if (h->fmt_key) {
+            std::lock_guard<std::mutex> g(seg.fmt_mu);
+            auto it = seg.fmt_cache.find(h->fmt_key);
+            if (it != seg.fmt_cache.end())
+                fmt_s = it->second;
+        }
+        if (h->fmt_key)
+            fmt = fmt_s.c_str();
+        int64_t *ret = (int64_t *)(slot + GF_SLOT_RET_OFF);
+        const uint8_t *end = slot + seg.slot_bytes;
+        if (op == GF_OP_PRINTF) {
+            /* all lanes of a slot share one format: format them into one buffer and write it once */
+            std::string out;
+            uint64_t stream = 0;
+            for (uint32_t l = 0; l < nl && l < 32; l++) {
+                const gf_rec_hdr *rh = (const gf_rec_hdr *)pay;
+                if (pay + sizeof(gf_rec_hdr) > end || rh->bytes < sizeof(gf_rec_hdr) || pay + rh->bytes > end) {
+                    ret[l] = -1;
+                    continue;
+                }
+                uint64_t st = 0;
+                ret[l] = fmt ? do_printf(fmt, pay, out, &st) : -1;
+                if (l == 0)
+                    stream = st;
+                else if (st != stream) {       /* lanes writing to different streams */
+                    emit(stream, out);
+                    out.clear();
+                    stream = st;
+                }
+                pay += rh->bytes;
+            }
+            if (!file_of(stream))
+                for (uint32_t l = 0; l < nl && l < 32; l++)
+                    ret[l] = -1;
+            else
+                emit(stream, out);
+        } else {
+            for (uint32_t l = 0; l < nl && l < 32; l++) {
+                const gf_rec_hdr *rh = (const gf_rec_hdr *)pay;
+                if (pay + sizeof(gf_rec_hdr) > end || rh->bytes < sizeof(gf_rec_hdr) || pay + rh->bytes > end) {
+                    ret[l] = -1;
+                    continue;
+                }
+                ret[l] = call(op, fmt, pay);
+                pay += rh->bytes;
+            }
+        }
+        const uint64_t dt = now_ns() - t0;
+        h->t_host_ns = dt;
+        stats.slots++;
+        stats.records += nl;
+        stats.ns += dt;
+        stats.per_op[op < GF_NSTAT ? op : 0] += nl;
+        seg.served[s] = t + 1;
+        release_store(&h->seq, t + 2);
+        served++;
+    }
+    /* advance this thread's head over tickets whose slots the device has released */
+    uint64_t hd = seg.head[tid];
+    for (uint32_t k = 0; k < N; k += nthr) {
+        const uint32_t s = (uint32_t)(hd % N);
+        if (seg.served[s] != hd + 1)
+            break;
+        hd += nthr;
+    }
+    seg.head[tid] = hd;
+    return served;
+}
+
+} // namespace gfh

@@ -1,0 +1,125 @@
+/*
+ * Host RPC server: the paper's single RPC thread next to the offload runtime
+ * (Sec. 3.1, Fig. 2) and its generated landing pads (Sec. 3.2, Fig. 4b).
+ *
+ * The server owns no CUDA state: ring segments are plain memory (pinned and
+ * device-mapped in production, ordinary memory when CPU threads stand in for
+ * the device in tests), and device memory is reached only through the DMA and
+ * intern callbacks.  Landing pads are keyed by opcode; printf-style calls are
+ * formatted by the real libc one conversion at a time with the C type that
+ * the conversion names, which is the per-signature non-variadic landing pad
+ * of the paper built at run time from the argument tags.
+ *
+ * Ordering: a segment is scanned from its lowest unserved ticket; published
+ * slots are served as found (out of ticket order when an earlier claimant is
+ * slow), and a slot's "done" is released only after its output has reached
+ * the stream, so one device thread's successive calls appear in program order.
+ */
+#ifndef GF_HOST_SERVER_H
+#define GF_HOST_SERVER_H
+
+#include <stdint.h>
+#include <stdio.h>
+#include <atomic>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../gf_layout.h"
+
+namespace gfh {
+
+struct Segment {
+    uint8_t *slots = nullptr;       /* host address of slot 0                        */
+    uint32_t nslots = 0, slot_bytes = 0;
+    uint32_t prog = 0;
+    std::atomic<bool> active{false};
+    /* per server-thread scan state */
+    std::vector<uint64_t> head;     /* lowest unserved ticket per server thread       */
+    std::vector<uint64_t> served;   /* ticket last served in each slot (+1; 0 = none) */
+    std::unordered_map<uint64_t, std::string> fmt_cache;   /* fmt_key -> format */
+    std::mutex fmt_mu;
+    void reset(uint32_t nthreads);
+};
+
+/* Streams a device range to `sink` chunk by chunk (fwrite DMA); returns the
+ * bytes the sink accepted.  The sink returns false to stop. */
+typedef std::function<bool(const void *chunk, uint64_t n)> sink_fn;
+typedef std::function<uint64_t(uint64_t dev_src, uint64_t bytes, const sink_fn &sink)> d2h_fn;
+/* Fills a device range from `source` chunk by chunk (fread DMA); the source
+ * returns how many bytes it produced (fewer ends the transfer). */
+typedef std::function<uint64_t(void *buf, uint64_t want)> source_fn;
+typedef std::function<uint64_t(uint64_t dev_dst, uint64_t bytes, const source_fn &src)> h2d_fn;
+/* returns a device-readable address of a stable copy of s (getenv interning) */
+typedef std::function<uint64_t(const std::string &s)> intern_fn;
+typedef int64_t (*user_fn)(void *user, uint32_t opcode, void *rec);
+
+struct HostStats {
+    std::atomic<uint64_t> slots{0}, records{0}, ns{0}, dma_bytes{0};
+    std::atomic<uint64_t> per_op[GF_NSTAT];
+    HostStats()
+    {
+        for (auto &x : per_op)
+            x = 0;
+    }
+};
+
+class Server {
+  public:
+    Server();
+    ~Server();
+    void set_stdout(FILE *f);
+    void set_dma(d2h_fn d2h, h2d_fn h2d);
+    void set_intern(intern_fn f) { intern_ = f; }
+    int register_user(uint32_t opcode, user_fn fn, void *user);
+
+    /* serve every published slot of `seg` that belongs to server thread `tid`
+     * of `nthreads`; returns the number of slots served */
+    int poll(Segment &seg, uint32_t tid, uint32_t nthreads);
+
+    /* close FILE*s the programs left open */
+    void close_all();
+    HostStats stats;
+
+    /* one landing pad: exposed for tests that decode a record by hand */
+    int64_t call(uint32_t opcode, const char *fmt, const uint8_t *rec);
+
+  private:
+    int64_t do_printf(const char *fmt, const uint8_t *rec, std::string &out, uint64_t *stream);
+    FILE *file_of(uint64_t h);
+    void emit(uint64_t stream, const std::string &s);
+
+    FILE *out_ = stdout;
+    std::mutex out_mu_;
+    std::mutex files_mu_;
+    std::set<uint64_t> files_;
+    d2h_fn d2h_;
+    h2d_fn h2d_;
+    intern_fn intern_;
+    std::mutex intern_mu_;
+    std::map<std::string, uint64_t> interned_;
+    std::mutex user_mu_;
+    std::map<uint32_t, std::pair<user_fn, void *>> user_;
+};
+
+/* record accessors (shared with tests) */
+struct RecView {
+    const uint8_t *base;
+    uint32_t bytes, nargs;
+    const uint8_t *tags;
+    const uint64_t *words;
+    const uint8_t *tail;
+    explicit RecView(const uint8_t *r);
+    uint8_t tag(uint32_t k) const { return tags[k]; }
+    uint64_t word(uint32_t k) const { return words[k]; }
+    const char *str(uint32_t k) const { return (const char *)(tail + (uint32_t)(words[k] & 0xffffffffu)); }
+    uint32_t blob_len(uint32_t k) const { return (uint32_t)(words[k] >> 32); }
+    uint8_t *blob(uint32_t k) const { return (uint8_t *)(tail + (uint32_t)(words[k] & 0xffffffffu)); }
+};
+
+} // namespace gfh
+#endif

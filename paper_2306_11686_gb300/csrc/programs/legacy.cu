@@ -1,0 +1,113 @@
+/*
+ * Legacy-style programs run whole on the GPU (paper Sec. 1: the CPU program
+ * is not restructured; its serial part runs on one thread, its parallel loops
+ * on the whole device, its libc calls through RPC or the device libc).
+ *
+ * Each is the device twin of a serial C program; the same computation in
+ * plain C with the real libc is what a run must reproduce.
+ */
+#include "../gf_device.cuh"
+
+/*
+ * axpy_sum N out_path            buffers: 0 = x (N doubles), 1 = y (N doubles, updated)
+ *
+ *   y[i] = 2.5*x[i] + y[i] over [0, N), printf("%d %.17g\n", i, y[i]) when i % 1024 == 0;
+ *   s = sum of y (worksharing reduction), printf("sum %.17g\n", s);
+ *   fopen / fwrite(y) / fclose.
+ */
+GF_MAIN(axpy_sum)(int argc, char **argv)
+{
+    if (argc < 3)
+        return 2;
+    const long long n = gf_atoll(argv[1]);
+    const double *x = (const double *)gf_buffer(0);
+    double *y = (double *)gf_buffer(1);
+    if (n < 0 || (n > 0 && (!x || !y)) || gf_buffer_bytes(0) < (uint64_t)n * 8 ||
+        gf_buffer_bytes(1) < (uint64_t)n * 8)
+        return 2;
+    int rc = gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) {
+        const double v = 2.5 * x[i] + y[i];
+        y[i] = v;
+        if (i % 1024 == 0)
+            gf_printf("%d %.17g\n", (int)i, v);
+    });
+    if (rc)
+        return 10;
+    double s = 0.0;
+    rc = gf_reduce<double, GF_RED_SUM>(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) { return y[i]; }, &s);
+    if (rc)
+        return 11;
+    gf_printf("sum %.17g\n", s);
+    GF_FILE f = gf_fopen(argv[2], "wb");
+    if (!f)
+        return 3;
+    if (gf_fwrite(y, sizeof(double), (size_t)n, f) != (size_t)n)
+        return 3;
+    gf_fclose(f);
+    return 0;
+}
+
+/*
+ * jacobi n sweeps out_path       buffers: 0 = input grid (n^3 doubles, i fastest)
+ *
+ * Laplace Jacobi sweeps with the six-neighbour average, boundary written as 0,
+ * a fresh grid from the device heap every sweep (old one freed after the
+ * swap), the max residual over the interior fused into the sweep as a max
+ * reduction, one printf per sweep, the final grid fwrite'd.
+ */
+GF_MAIN(jacobi)(int argc, char **argv)
+{
+    if (argc < 4)
+        return 2;
+    const long long n = gf_atoll(argv[1]);
+    const int sweeps = (int)gf_atoll(argv[2]);
+    const double *u0 = (const double *)gf_buffer(0);
+    const uint64_t cells = (uint64_t)n * n * n;
+    if (n < 1 || n > 1290 || !u0 || gf_buffer_bytes(0) < cells * 8)
+        return 2;
+    const uint32_t nn = (uint32_t)n, sk = nn * nn;
+    const double *u = u0;
+    double *owned = nullptr;
+    for (int s = 1; s <= sweeps; s++) {
+        double *un = (double *)gf_malloc(cells * sizeof(double));
+        if (!un) {
+            gf_printf("jacobi: out of device heap at sweep %d\n", s);
+            return 4;
+        }
+        double res = 0.0;
+        int rc = gf_reduce<double, GF_RED_MAX>(
+            0, (int64_t)cells, GF_SCHED_STATIC, 1,
+            [=](int64_t c64) -> double {
+                const uint32_t c = (uint32_t)c64;
+                const uint32_t i = c % nn, jk = c / nn, j = jk % nn, k = jk / nn;
+                if (i == 0 || j == 0 || k == 0 || i == nn - 1 || j == nn - 1 || k == nn - 1) {
+                    un[c] = 0.0;
+                    return 0.0;
+                }
+                double v = u[c - 1] + u[c + 1];
+                v = v + u[c - nn];
+                v = v + u[c + nn];
+                v = v + u[c - sk];
+                v = v + u[c + sk];
+                v = v / 6.0;
+                un[c] = v;
+                return fabs(v - u[c]);
+            },
+            &res);
+        if (rc)
+            return 10;
+        gf_printf("%d %.17g\n", s, res);
+        if (owned)
+            gf_free(owned);
+        owned = un;
+        u = un;
+    }
+    GF_FILE f = gf_fopen(argv[3], "wb");
+    if (!f)
+        return 3;
+    const size_t w = gf_fwrite(u, sizeof(double), (size_t)cells, f);
+    gf_fclose(f);
+    if (owned)
+        gf_free(owned);
+    return w == cells ? 0 : 3;
+}

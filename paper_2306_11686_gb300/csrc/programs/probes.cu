@@ -1,0 +1,250 @@
+/*
+ * Small programs that expose one runtime mechanism each, for the GPU tests:
+ * schedules, reductions, the cross-block barrier, RPC landing pads, the heap
+ * audit and the bounded-wait error path.
+ */
+#include "../gf_device.cuh"
+
+/* sched_probe b e sched chunk      buffers: 0 = int32 hits[e-b], 1 = int64 owner[e-b], 2 = int64 info[2]
+ * Every iteration records which continuous thread id ran it. */
+GF_MAIN(sched_probe)(int argc, char **argv)
+{
+    if (argc < 5)
+        return 2;
+    const long long b = gf_atoll(argv[1]), e = gf_atoll(argv[2]);
+    const int sched = (int)gf_atoll(argv[3]);
+    const long long chunk = gf_atoll(argv[4]);
+    int *hits = (int *)gf_buffer(0);
+    long long *owner = (long long *)gf_buffer(1);
+    long long *info = (long long *)gf_buffer(2);
+    if (!hits || !owner || !info)
+        return 2;
+    info[0] = 0;
+    int rc = gf_parallel_for(b, e, sched, chunk, [=](int64_t i) {
+        atomicAdd(&hits[i - b], 1);
+        owner[i - b] = gf_thread_num();
+        if (i == b)
+            info[0] = gf_num_threads();
+    });
+    info[1] = gf_num_threads();   /* the initial thread outside a region: a team of 1 */
+    return rc ? 10 : 0;
+}
+
+/* reduce_probe n sched chunk       buffers: 0 = double x[n], 1 = int64 v[n], 2 = out[6] */
+GF_MAIN(reduce_probe)(int argc, char **argv)
+{
+    if (argc < 4)
+        return 2;
+    const long long n = gf_atoll(argv[1]);
+    const int sched = (int)gf_atoll(argv[2]);
+    const long long chunk = gf_atoll(argv[3]);
+    const double *x = (const double *)gf_buffer(0);
+    const long long *v = (const long long *)gf_buffer(1);
+    uint64_t *out = (uint64_t *)gf_buffer(2);
+    if (!x || !v || !out)
+        return 2;
+    double d;
+    long long l;
+    int rc = 0;
+    rc |= gf_reduce<double, GF_RED_SUM>(0, n, sched, chunk, [=](int64_t i) { return x[i]; }, &d);
+    out[0] = __double_as_longlong(d);
+    rc |= gf_reduce<double, GF_RED_MIN>(0, n, sched, chunk, [=](int64_t i) { return x[i]; }, &d);
+    out[1] = __double_as_longlong(d);
+    rc |= gf_reduce<double, GF_RED_MAX>(0, n, sched, chunk, [=](int64_t i) { return x[i]; }, &d);
+    out[2] = __double_as_longlong(d);
+    rc |= gf_reduce<long long, GF_RED_SUM>(0, n, sched, chunk, [=](int64_t i) { return v[i]; }, &l);
+    out[3] = (uint64_t)l;
+    rc |= gf_reduce<long long, GF_RED_MIN>(0, n, sched, chunk, [=](int64_t i) { return v[i]; }, &l);
+    out[4] = (uint64_t)l;
+    rc |= gf_reduce<long long, GF_RED_MAX>(0, n, sched, chunk, [=](int64_t i) { return v[i]; }, &l);
+    out[5] = (uint64_t)l;
+    return rc ? 10 : 0;
+}
+
+/* barrier_probe rounds             buffers: 0 = int64 a[T], 1 = int64 errors[1]
+ * Each worker writes its slot, crosses the grid barrier, and reads a slot
+ * written by a thread of another block; any stale value counts an error. */
+GF_MAIN(barrier_probe)(int argc, char **argv)
+{
+    if (argc < 2)
+        return 2;
+    const int rounds = (int)gf_atoll(argv[1]);
+    long long *a = (long long *)gf_buffer(0);
+    unsigned long long *err = (unsigned long long *)gf_buffer(1);
+    if (!a || !err)
+        return 2;
+    const int T = (int)(gfd::s_st->nblocks * gfd::s_st->block_dim - 32);
+    if (gf_buffer_bytes(0) < (uint64_t)T * 8)
+        return 3;
+    int rc = gf_parallel_for(0, T, GF_SCHED_STATIC, 1, [=](int64_t t) {
+        const int64_t other = (t + 1 + 3 * GF_BLOCK) % T;
+        for (int r = 0; r < rounds; r++) {
+            a[t] = (long long)r * 1000003ll + t;
+            __threadfence();
+            if (gf_barrier())
+                atomicAdd(err, 1000000ull);
+            if (*(volatile long long *)&a[other] != (long long)r * 1000003ll + other)
+                atomicAdd(err, 1ull);
+            if (gf_barrier())
+                atomicAdd(err, 1000000ull);
+        }
+    });
+    return rc ? 10 : 0;
+}
+
+/*
+ * rpc_probe path_small path_big nbig      buffers: 0 = int64 results[32], 1 = bytes big[nbig]
+ * Exercises every landing pad; results[] receives the host return values.
+ */
+GF_MAIN(rpc_probe)(int argc, char **argv)
+{
+    if (argc < 4)
+        return 2;
+    long long *res = (long long *)gf_buffer(0);
+    unsigned char *big = (unsigned char *)gf_buffer(1);
+    const long long nbig = gf_atoll(argv[3]);
+    if (!res || !big)
+        return 2;
+    int k = 0;
+    res[k++] = gf_printf("int %d %i %u %x %X %o|\n", -42, 7, 4000000000u, 255u, 3054u, 8u);
+    res[k++] = gf_printf("long %ld %lld %llu %lx\n", -5000000000l, 123456789012345ll, 18446744073709551615ull,
+                         0xdeadbeefcafeul);
+    res[k++] = gf_printf("dbl %f %e %g %.17g %10.3f|%-8.2e|%+.0f\n", 3.14159, -1.5e-300, 1e100, 0.1, 2.5, 12345.678, 2.5);
+    res[k++] = gf_printf("str [%s] [%10s] [%-6s] [%.3s] %c%c %%\n", "hello", "right", "left", "truncate", 'o', 'k');
+    res[k++] = gf_printf("star [%*d] [%-*d] [%.*f]\n", 6, 42, 5, 7, 3, 1.0 / 3.0);
+    res[k++] = gf_printf("no args\n");
+    GF_FILE f = gf_fopen(argv[1], "w");
+    res[k++] = f != 0;
+    res[k++] = gf_fprintf(f, "to file %d %s\n", 99, "ok");
+    const char blob[] = "0123456789abcdef";
+    res[k++] = (long long)gf_fwrite(blob, 1, 16, f);
+    res[k++] = gf_fclose(f);
+    GF_FILE g = gf_fopen(argv[2], "wb");
+    res[k++] = (long long)gf_fwrite(big, 1, (size_t)nbig, g);   /* DMA path */
+    res[k++] = gf_fclose(g);
+    /* read both back: small inline and large DMA */
+    char back[64];
+    for (int q = 0; q < 64; q++)
+        back[q] = 0;
+    GF_FILE r = gf_fopen(argv[1], "r");
+    res[k++] = (long long)gf_fread(back, 1, 20, r);
+    gf_fclose(r);
+    long long sum = 0;
+    for (int q = 0; q < 20; q++)
+        sum = sum * 31 + (unsigned char)back[q];
+    res[k++] = sum;
+    for (long long q = 0; q < nbig; q++)
+        big[q] = 0;
+    GF_FILE r2 = gf_fopen(argv[2], "rb");
+    res[k++] = (long long)gf_fread(big, 1, (size_t)nbig, r2);
+    gf_fclose(r2);
+    const char *hv = gf_getenv("GF_PROBE_VAR");
+    res[k++] = hv ? (long long)gf_strlen(hv) : -1;
+    res[k++] = hv ? (long long)hv[0] : -1;
+    res[k++] = gf_getenv("GF_PROBE_UNSET_VAR") ? 1 : 0;
+    const long long c0 = gf_clock();
+    const long long c1 = gf_clock();
+    res[k++] = c1 >= c0 ? 1 : 0;
+    res[k++] = gf_fopen("/nonexistent-dir/x", "r") == 0 ? 1 : 0;
+    res[k++] = k;
+    return 0;
+}
+
+/* rpc_storm nthreads calls          every iteration prints `calls` lines "t <i> k <k> v <double>" */
+GF_MAIN(rpc_storm)(int argc, char **argv)
+{
+    if (argc < 3)
+        return 2;
+    const long long n = gf_atoll(argv[1]);
+    const int calls = (int)gf_atoll(argv[2]);
+    unsigned long long *bad = (unsigned long long *)gf_buffer(0);
+    int rc = gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) {
+        for (int k = 0; k < calls; k++) {
+            const int r = gf_printf("t %lld k %d v %.6e\n", (long long)i, k, (double)i * 0.5 + k);
+            if (r <= 0 && bad)
+                atomicAdd(bad, 1ull);
+        }
+    });
+    return rc ? 10 : 0;
+}
+
+/* heap_audit n per                  buffers: 0 = uint32 sizes[n*per], 1 = uint64 ptrs[n*per], 2 = uint64 info[4]
+ * Every iteration allocates `per` blocks and keeps them live; the host audits
+ * the (ptr, size) set, then a second region frees everything and a third
+ * allocates again to check reuse. */
+GF_MAIN(heap_audit)(int argc, char **argv)
+{
+    if (argc < 3)
+        return 2;
+    const long long n = gf_atoll(argv[1]);
+    const int per = (int)gf_atoll(argv[2]);
+    const unsigned *sz = (const unsigned *)gf_buffer(0);
+    unsigned long long *ptr = (unsigned long long *)gf_buffer(1);
+    unsigned long long *info = (unsigned long long *)gf_buffer(2);
+    if (!sz || !ptr || !info)
+        return 2;
+    int rc = gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) {
+        for (int j = 0; j < per; j++) {
+            const unsigned s = sz[i * per + j];
+            unsigned long long *p = (unsigned long long *)gf_malloc(s);
+            ptr[i * per + j] = (unsigned long long)p;
+            if (p) {
+                p[0] = (unsigned long long)(i * per + j);
+                p[(s / 8) - 1] = ~(unsigned long long)(i * per + j);
+            }
+        }
+    });
+    /* every block still holds its tags: nobody else was handed overlapping memory */
+    unsigned long long bad = 0;
+    gf_reduce<long long, GF_RED_SUM>(0, n * per, GF_SCHED_STATIC, 1, [=](int64_t q) -> long long {
+        unsigned long long *p = (unsigned long long *)ptr[q];
+        if (!p)
+            return 0;
+        const unsigned s = sz[q];
+        return (p[0] != (unsigned long long)q || p[(s / 8) - 1] != ~(unsigned long long)q) ? 1 : 0;
+    }, (long long *)&bad);
+    info[0] = bad;
+    info[1] = gfd::s_st->heap.live_bytes;
+    rc |= gf_parallel_for(0, n * per, GF_SCHED_STATIC, 1, [=](int64_t q) { gf_free((void *)ptr[q]); });
+    info[2] = gfd::s_st->heap.live_bytes;
+    /* allocate again: freed blocks come back */
+    unsigned long long again = 0;
+    gf_reduce<long long, GF_RED_SUM>(0, n * per, GF_SCHED_STATIC, 1, [=](int64_t q) -> long long {
+        void *p = gf_malloc(sz[q]);
+        const long long ok = p ? 1 : 0;
+        gf_free(p);
+        return ok;
+    }, (long long *)&again);
+    info[3] = again;
+    return rc ? 10 : 0;
+}
+
+/* heap_big nbytes count            initial-thread large allocations; buffer 0 = uint64 ptrs[count] */
+GF_MAIN(heap_big)(int argc, char **argv)
+{
+    if (argc < 3)
+        return 2;
+    const unsigned long long nb = (unsigned long long)gf_atoll(argv[1]);
+    const int count = (int)gf_atoll(argv[2]);
+    unsigned long long *out = (unsigned long long *)gf_buffer(0);
+    for (int k = 0; k < count; k++)
+        out[k] = (unsigned long long)gf_malloc(nb);
+    gf_free((void *)out[1]);     /* hole in the middle, then reuse it */
+    out[count] = (unsigned long long)gf_malloc(nb);
+    for (int k = 0; k < count; k++)
+        if (k != 1)
+            gf_free((void *)out[k]);
+    gf_free((void *)out[count]);
+    out[count + 1] = (unsigned long long)gf_malloc(nb * count);   /* everything merged back */
+    gf_free((void *)out[count + 1]);
+    gf_free((void *)0x1234);     /* foreign pointer: counted, ignored */
+    return 0;
+}
+
+/* rpc_timeout                      the host does not serve: the call must come back with GF_ETIMEDOUT */
+GF_MAIN(rpc_timeout)(int argc, char **argv)
+{
+    int st = 0;
+    gfd::rpc(GF_OP_CLOCK, nullptr, &st);
+    return st == GF_ETIMEDOUT ? 1 : (st == GF_OK ? 0 : 2);
+}

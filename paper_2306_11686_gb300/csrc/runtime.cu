@@ -1,0 +1,801 @@
+/*
+ * Host runtime: the C ABI of include/gf.h.
+ *
+ * The loader part follows the paper's main wrapper (Sec. 3.1): argv and the
+ * mapped buffers go to the device, the RPC server runs, main starts on the
+ * GPU.  GB300 specifics:
+ *  - the ring lives in pinned host memory mapped into the device address space
+ *    (cudaHostAllocMapped); on Grace-Blackwell the GPU reaches it coherently
+ *    over NVLink-C2C, so hand-offs are single release/acquire words instead of
+ *    the paper's managed-memory page traffic;
+ *  - bulk fwrite/fread payloads move by copy-engine DMA on a separate stream,
+ *    double-buffered through pinned staging, while the program's grid keeps
+ *    running (no SM time spent copying);
+ *  - each program instance owns a ring segment, a heap arena and its state, so
+ *    concurrent programs (serving) are isolated and admission is a matter of a
+ *    free instance.
+ */
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "gf.h"
+#include "gf_layout.h"
+#include "gf_program.h"
+#include "host/server.h"
+
+#define GF_MAX_BLOCKS_PER_SM 32
+#define GF_ARGV_BYTES (64u * 1024u)
+#define GF_DMA_CHUNK (16ull << 20)
+#define GF_INTERN_BYTES (1u << 20)
+#define GF_BLOCK_THREADS 256
+
+/* ------------------------------------------------------------------ registry */
+struct ProgEntry {
+    std::string name;
+    gf_launch_fn launch;
+    gf_occ_fn occ;
+};
+static std::mutex &reg_mu()
+{
+    static std::mutex m;
+    return m;
+}
+static std::vector<ProgEntry> &registry()
+{
+    static std::vector<ProgEntry> r;
+    return r;
+}
+
+extern "C" __attribute__((visibility("default"))) int gf_program_register(const char *name, gf_launch_fn launch,
+                                                                           gf_occ_fn occ)
+{
+    std::lock_guard<std::mutex> g(reg_mu());
+    registry().push_back({name, launch, occ});
+    return (int)registry().size() - 1;
+}
+
+/* ------------------------------------------------------------------ context */
+struct Staged {
+    void *host;
+    void *dev;
+    uint64_t bytes;
+    uint32_t dir;
+    bool owned;
+};
+
+struct Instance {
+    int idx = 0;
+    std::atomic<bool> busy{false};
+    gf_state *d_state = nullptr;
+    void *d_partials = nullptr;
+    void *d_fmt = nullptr;
+    uint8_t *d_heap = nullptr;
+    void *d_meta = nullptr, *d_heads = nullptr, *d_cur = nullptr, *d_ext = nullptr, *d_lsize = nullptr;
+    uint32_t nslabs = 0, npages = 0;
+    uint64_t slab_bytes = 0, large_bytes = 0;
+    char *d_argv = nullptr;
+    std::vector<char> h_argv;
+    gf_state h_init;     /* initial state copied to the device at launch */
+    gf_state h_final;    /* state read back after the program ends       */
+    uint64_t h_ext0 = 0;
+    gfh::Segment seg;
+    cudaEvent_t ev_done = nullptr;
+};
+
+struct gf_handle {
+    gf_ctx *ctx;
+    Instance *inst;
+    cudaStream_t stream;
+    std::vector<Staged> staged;
+    uint32_t grid, block;
+    bool finished = false;
+};
+
+struct gf_ctx {
+    gf_config cfg;
+    int device = 0, nsm = 0;
+    uint8_t *ring_host = nullptr;
+    uint64_t ring_dev = 0;
+    size_t ring_bytes = 0;
+    std::vector<Instance *> inst;
+    gfh::Server server;
+    std::vector<std::thread> threads;
+    std::atomic<bool> stop{false};
+    std::atomic<int> nactive{0};
+    std::mutex act_mu;
+    std::condition_variable act_cv;
+    cudaStream_t own_stream = nullptr, dma_stream = nullptr;
+    void *dma_stage[2] = {nullptr, nullptr};
+    cudaEvent_t dma_ev[2] = {nullptr, nullptr};
+    std::mutex dma_mu;
+    uint8_t *intern_host = nullptr;
+    uint64_t intern_dev = 0;
+    size_t intern_used = 0;
+    FILE *out = stdout;
+    bool own_out = false;
+    std::mutex stats_mu;
+    gf_stats last;
+};
+
+static int cuda_err(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return GF_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return GF_ENOMEM;
+    return GF_ECUDA;
+}
+#define GF_CK(x)                                                                                    \
+    do {                                                                                            \
+        cudaError_t _e = (x);                                                                       \
+        if (_e != cudaSuccess) {                                                                    \
+            fprintf(stderr, "gf: %s failed: %s (%s:%d)\n", #x, cudaGetErrorString(_e), __FILE__, __LINE__); \
+            return cuda_err(_e);                                                                    \
+        }                                                                                           \
+    } while (0)
+
+extern "C" GF_API void gf_config_default(gf_config *c)
+{
+    memset(c, 0, sizeof *c);
+    c->heap_bytes = 4ull << 30;
+    c->heap_small_pct = 50;
+    c->ring_slots = 4096;
+    c->slot_bytes = 4096;
+    c->aggregate = 1;
+    c->server_threads = 1;
+    c->max_programs = 1;
+    c->grid = 0;
+    c->timeout_ns = 30ll * 1000 * 1000 * 1000;
+    c->stream = nullptr;
+    c->stdout_path = nullptr;
+    c->fmt_cache = 4096;
+    c->device = -1;
+}
+
+extern "C" GF_API const char *gf_strerror(int e)
+{
+    switch (e) {
+    case GF_OK: return "ok";
+    case GF_EINVAL: return "invalid argument";
+    case GF_ENOMEM: return "out of memory";
+    case GF_ERING: return "no RPC ring slot became free in time";
+    case GF_ETIMEDOUT: return "timed out waiting for the host or for other threads";
+    case GF_EHOST: return "host landing pad failed";
+    case GF_ECUDA: return "CUDA runtime error";
+    case GF_ENOENT: return "no such program";
+    case GF_EBUSY: return "no free program instance";
+    default: return "unknown error";
+    }
+}
+
+static bool pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+/* ------------------------------------------------------------------ DMA */
+static uint64_t dma_d2h(gf_ctx *c, uint64_t dev, uint64_t bytes, const gfh::sink_fn &sink)
+{
+    std::lock_guard<std::mutex> g(c->dma_mu);
+    uint64_t pend[2] = {0, 0}, off = 0, delivered = 0;
+    int b = 0;
+    auto issue = [&](int k) {
+        const uint64_t n = std::min<uint64_t>(GF_DMA_CHUNK, bytes - off);
+        pend[k] = 0;
+        if (!n)
+            return true;
+        if (cudaMemcpyAsync(c->dma_stage[k], (const void *)(dev + off), n, cudaMemcpyDeviceToHost, c->dma_stream) !=
+                cudaSuccess ||
+            cudaEventRecord(c->dma_ev[k], c->dma_stream) != cudaSuccess)
+            return false;
+        pend[k] = n;
+        off += n;
+        return true;
+    };
+    if (!issue(0))
+        return 0;
+    while (pend[b]) {
+        if (!issue(1 - b))
+            break;
+        if (cudaEventSynchronize(c->dma_ev[b]) != cudaSuccess)
+            break;
+        if (!sink(c->dma_stage[b], pend[b]))
+            break;
+        delivered += pend[b];
+        pend[b] = 0;
+        b = 1 - b;
+    }
+    cudaStreamSynchronize(c->dma_stream);
+    return delivered;
+}
+
+static uint64_t dma_h2d(gf_ctx *c, uint64_t dev, uint64_t bytes, const gfh::source_fn &src)
+{
+    std::lock_guard<std::mutex> g(c->dma_mu);
+    uint64_t off = 0;
+    int b = 0;
+    bool inflight[2] = {false, false};
+    while (off < bytes) {
+        if (inflight[b]) {
+            cudaEventSynchronize(c->dma_ev[b]);
+            inflight[b] = false;
+        }
+        const uint64_t want = std::min<uint64_t>(GF_DMA_CHUNK, bytes - off);
+        const uint64_t got = src(c->dma_stage[b], want);
+        if (got) {
+            if (cudaMemcpyAsync((void *)(dev + off), c->dma_stage[b], got, cudaMemcpyHostToDevice, c->dma_stream) !=
+                    cudaSuccess ||
+                cudaEventRecord(c->dma_ev[b], c->dma_stream) != cudaSuccess)
+                break;
+            inflight[b] = true;
+            off += got;
+        }
+        if (got != want)
+            break;
+        b = 1 - b;
+    }
+    cudaStreamSynchronize(c->dma_stream);
+    return off;
+}
+
+/* ------------------------------------------------------------------ server threads */
+static void server_main(gf_ctx *c, uint32_t tid, uint32_t nthr)
+{
+    uint32_t idle = 0;
+    while (!c->stop.load(std::memory_order_relaxed)) {
+        int n = 0;
+        for (Instance *in : c->inst)
+            if (in->seg.active.load(std::memory_order_acquire))
+                n += c->server.poll(in->seg, tid, nthr);
+        if (n) {
+            idle = 0;
+            continue;
+        }
+        if (c->nactive.load(std::memory_order_acquire) == 0) {
+            std::unique_lock<std::mutex> lk(c->act_mu);
+            c->act_cv.wait_for(lk, std::chrono::milliseconds(5),
+                               [&] { return c->stop.load() || c->nactive.load() > 0; });
+        } else if (++idle > 4096) {
+            std::this_thread::yield();
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ init / finalize */
+static int inst_alloc(gf_ctx *c, Instance *in)
+{
+    const gf_config &cf = c->cfg;
+    GF_CK(cudaMalloc((void **)&in->d_state, sizeof(gf_state)));
+    GF_CK(cudaMalloc(&in->d_partials, (size_t)c->nsm * GF_MAX_BLOCKS_PER_SM * 16));
+    GF_CK(cudaMalloc(&in->d_fmt, (size_t)cf.fmt_cache * 8));
+    GF_CK(cudaMalloc((void **)&in->d_argv, GF_ARGV_BYTES));
+    /* heap arena: [small slabs | large pages] */
+    const uint64_t slab = 1ull << GF_SLAB_SHIFT, page = 1ull << GF_PAGE_SHIFT;
+    in->slab_bytes = (cf.heap_bytes * cf.heap_small_pct / 100) / slab * slab;
+    in->large_bytes = (cf.heap_bytes - in->slab_bytes) / page * page;
+    in->nslabs = (uint32_t)(in->slab_bytes / slab);
+    in->npages = (uint32_t)(in->large_bytes / page);
+    if (in->slab_bytes + in->large_bytes)
+        GF_CK(cudaMalloc((void **)&in->d_heap, in->slab_bytes + in->large_bytes));
+    GF_CK(cudaMalloc(&in->d_meta, (size_t)std::max<uint32_t>(in->nslabs, 1) * 16));
+    GF_CK(cudaMalloc(&in->d_heads, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 8));
+    GF_CK(cudaMalloc(&in->d_cur, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 4));
+    GF_CK(cudaMalloc(&in->d_ext, (size_t)GF_LARGE_EXT_MAX * 8));
+    GF_CK(cudaMalloc(&in->d_lsize, (size_t)std::max<uint32_t>(in->npages, 1) * 4));
+    GF_CK(cudaEventCreateWithFlags(&in->ev_done, cudaEventDisableTiming));
+    in->seg.nslots = cf.ring_slots;
+    in->seg.slot_bytes = cf.slot_bytes;
+    in->seg.prog = (uint32_t)in->idx;
+    in->seg.slots = c->ring_host + (size_t)in->idx * cf.ring_slots * cf.slot_bytes;
+    return GF_OK;
+}
+
+static void inst_free(Instance *in)
+{
+    cudaFree(in->d_state);
+    cudaFree(in->d_partials);
+    cudaFree(in->d_fmt);
+    cudaFree(in->d_argv);
+    cudaFree(in->d_heap);
+    cudaFree(in->d_meta);
+    cudaFree(in->d_heads);
+    cudaFree(in->d_cur);
+    cudaFree(in->d_ext);
+    cudaFree(in->d_lsize);
+    if (in->ev_done)
+        cudaEventDestroy(in->ev_done);
+}
+
+extern "C" GF_API int gf_finalize(gf_ctx *c)
+{
+    if (!c)
+        return GF_OK;
+    for (Instance *in : c->inst)
+        if (in->busy.load() && in->ev_done)
+            cudaEventSynchronize(in->ev_done);
+    c->stop = true;
+    c->act_cv.notify_all();
+    for (auto &t : c->threads)
+        t.join();
+    c->server.close_all();
+    if (c->own_out && c->out)
+        fclose(c->out);
+    for (Instance *in : c->inst) {
+        inst_free(in);
+        delete in;
+    }
+    if (c->ring_host)
+        cudaFreeHost(c->ring_host);
+    if (c->intern_host)
+        cudaFreeHost(c->intern_host);
+    for (int k = 0; k < 2; k++) {
+        if (c->dma_stage[k])
+            cudaFreeHost(c->dma_stage[k]);
+        if (c->dma_ev[k])
+            cudaEventDestroy(c->dma_ev[k]);
+    }
+    if (c->dma_stream)
+        cudaStreamDestroy(c->dma_stream);
+    if (c->own_stream)
+        cudaStreamDestroy(c->own_stream);
+    delete c;
+    return GF_OK;
+}
+
+extern "C" GF_API int gf_init(const gf_config *cfg, gf_ctx **out)
+{
+    if (!out)
+        return GF_EINVAL;
+    *out = nullptr;
+    gf_config cf;
+    gf_config_default(&cf);
+    if (cfg)
+        cf = *cfg;
+    if (!pow2(cf.ring_slots) || cf.slot_bytes < 1024 || cf.slot_bytes % 64 || !pow2(cf.fmt_cache) ||
+        cf.max_programs < 1 || cf.max_programs > 1024 || cf.heap_small_pct > 100 || cf.timeout_ns <= 0)
+        return GF_EINVAL;
+    if (cf.server_threads && (!pow2(cf.server_threads) || cf.server_threads > cf.ring_slots))
+        return GF_EINVAL;
+    gf_ctx *c = new gf_ctx();
+    c->cfg = cf;
+    memset(&c->last, 0, sizeof c->last);
+    int rc = GF_OK;
+    auto fail = [&](int e) {
+        gf_finalize(c);
+        return e;
+    };
+    if (cf.device >= 0 && cudaSetDevice(cf.device) != cudaSuccess)
+        return fail(GF_ECUDA);
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        return fail(GF_ECUDA);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+    if (!coop)
+        return fail(GF_ECUDA);
+    size_t stack = 0;
+    cudaDeviceGetLimit(&stack, cudaLimitStackSize);
+    if (stack < 4096)
+        cudaDeviceSetLimit(cudaLimitStackSize, 4096);
+    /* ring: pinned, device-mapped host memory */
+    c->ring_bytes = (size_t)cf.ring_slots * cf.slot_bytes * cf.max_programs;
+    if (cudaHostAlloc((void **)&c->ring_host, c->ring_bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
+        return fail(GF_ENOMEM);
+    memset(c->ring_host, 0, c->ring_bytes);
+    void *rd = nullptr;
+    if (cudaHostGetDevicePointer(&rd, c->ring_host, 0) != cudaSuccess)
+        return fail(GF_ECUDA);
+    c->ring_dev = (uint64_t)rd;
+    if (cudaHostAlloc((void **)&c->intern_host, GF_INTERN_BYTES, cudaHostAllocMapped | cudaHostAllocPortable) !=
+        cudaSuccess)
+        return fail(GF_ENOMEM);
+    void *idv = nullptr;
+    cudaHostGetDevicePointer(&idv, c->intern_host, 0);
+    c->intern_dev = (uint64_t)idv;
+    for (int k = 0; k < 2; k++) {
+        if (cudaHostAlloc(&c->dma_stage[k], GF_DMA_CHUNK, cudaHostAllocPortable) != cudaSuccess)
+            return fail(GF_ENOMEM);
+        if (cudaEventCreateWithFlags(&c->dma_ev[k], cudaEventDisableTiming) != cudaSuccess)
+            return fail(GF_ECUDA);
+    }
+    if (cudaStreamCreateWithFlags(&c->dma_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(GF_ECUDA);
+    for (uint32_t k = 0; k < cf.max_programs; k++) {
+        Instance *in = new Instance();
+        in->idx = (int)k;
+        c->inst.push_back(in);
+        if ((rc = inst_alloc(c, in)) != GF_OK)
+            return fail(rc);
+    }
+    if (cf.stdout_path) {
+        c->out = fopen(cf.stdout_path, "w");
+        if (!c->out)
+            return fail(GF_EINVAL);
+        setvbuf(c->out, nullptr, _IOFBF, 4 << 20);
+        c->own_out = true;
+    }
+    c->server.set_stdout(c->out);
+    c->server.set_dma([c](uint64_t d, uint64_t n, const gfh::sink_fn &s) { return dma_d2h(c, d, n, s); },
+                      [c](uint64_t d, uint64_t n, const gfh::source_fn &s) { return dma_h2d(c, d, n, s); });
+    c->server.set_intern([c](const std::string &s) -> uint64_t {
+        if (c->intern_used + s.size() + 1 > GF_INTERN_BYTES)
+            return 0;
+        memcpy(c->intern_host + c->intern_used, s.c_str(), s.size() + 1);
+        const uint64_t a = c->intern_dev + c->intern_used;
+        c->intern_used += (s.size() + 16) & ~size_t(7);
+        return a;
+    });
+    for (uint32_t t = 0; t < cf.server_threads; t++)
+        c->threads.emplace_back(server_main, c, t, cf.server_threads);
+    *out = c;
+    return GF_OK;
+}
+
+extern "C" GF_API int gf_program_lookup(gf_ctx *c, const char *name, gf_program *out)
+{
+    if (!c || !name || !out)
+        return GF_EINVAL;
+    std::lock_guard<std::mutex> g(reg_mu());
+    for (size_t k = 0; k < registry().size(); k++)
+        if (registry()[k].name == name) {
+            *out = (gf_program)k;
+            return GF_OK;
+        }
+    return GF_ENOENT;
+}
+
+extern "C" GF_API int gf_rpc_register(gf_ctx *c, uint32_t opcode, gf_host_fn fn, void *user)
+{
+    if (!c || opcode < GF_OP_USER || !fn)
+        return GF_EINVAL;
+    return c->server.register_user(opcode, fn, user);
+}
+
+static int occupancy(gf_ctx *c, gf_program prog, uint32_t *per_sm)
+{
+    ProgEntry pe;
+    {
+        std::lock_guard<std::mutex> g(reg_mu());
+        if (prog < 0 || (size_t)prog >= registry().size())
+            return GF_ENOENT;
+        pe = registry()[prog];
+    }
+    int occ = pe.occ(GF_BLOCK_THREADS);
+    if (occ < 1)
+        return GF_ECUDA;
+    *per_sm = (uint32_t)std::min(occ, GF_MAX_BLOCKS_PER_SM);
+    return GF_OK;
+}
+
+extern "C" GF_API int gf_grid_info(gf_ctx *c, gf_program prog, uint32_t *sms, uint32_t *per_sm)
+{
+    if (!c || !sms || !per_sm)
+        return GF_EINVAL;
+    *sms = (uint32_t)c->nsm;
+    return occupancy(c, prog, per_sm);
+}
+
+/* ------------------------------------------------------------------ launch / wait */
+static void release_staged(gf_handle *h, bool copy_back)
+{
+    for (Staged &s : h->staged) {
+        if (copy_back && s.owned && (s.dir & GF_BUF_OUT))
+            cudaMemcpyAsync(s.host, s.dev, s.bytes, cudaMemcpyDeviceToHost, h->stream);
+    }
+    cudaStreamSynchronize(h->stream);
+    for (Staged &s : h->staged)
+        if (s.owned)
+            cudaFreeAsync(s.dev, h->stream);
+    h->staged.clear();
+}
+
+extern "C" GF_API int gf_launch(gf_ctx *c, gf_program prog, int argc, const char *const *argv, const gf_buf *bufs,
+                                int nbufs, void *stream, uint32_t grid, gf_handle **out)
+{
+    if (!c || !out || argc < 0 || nbufs < 0 || nbufs > GF_MAX_BUFS || (nbufs && !bufs) || (argc && !argv))
+        return GF_EINVAL;
+    *out = nullptr;
+    ProgEntry pe;
+    {
+        std::lock_guard<std::mutex> g(reg_mu());
+        if (prog < 0 || (size_t)prog >= registry().size())
+            return GF_ENOENT;
+        pe = registry()[prog];
+    }
+    uint32_t per_sm = 0;
+    int rc = occupancy(c, prog, &per_sm);
+    if (rc)
+        return rc;
+    const uint32_t full = per_sm * (uint32_t)c->nsm;
+    if (!grid)
+        grid = c->cfg.grid ? c->cfg.grid : std::max<uint32_t>(1, full / c->cfg.max_programs);
+    if (grid > full || grid > (uint32_t)c->nsm * GF_MAX_BLOCKS_PER_SM)
+        return GF_EINVAL;
+    /* argv block: pointer array then strings, all device addresses */
+    size_t need = (size_t)(argc + 1) * 8;
+    for (int k = 0; k < argc; k++)
+        need += strlen(argv[k]) + 1;
+    if (need > GF_ARGV_BYTES)
+        return GF_EINVAL;
+    /* admission: a free instance (its ring segment and heap arena) */
+    Instance *in = nullptr;
+    for (Instance *x : c->inst) {
+        bool f = false;
+        if (x->busy.compare_exchange_strong(f, true)) {
+            in = x;
+            break;
+        }
+    }
+    if (!in)
+        return GF_EBUSY;
+    gf_handle *h = new gf_handle();
+    h->ctx = c;
+    h->inst = in;
+    h->stream = (cudaStream_t)(stream ? stream : (c->cfg.stream ? c->cfg.stream : c->own_stream));
+    h->grid = grid;
+    h->block = GF_BLOCK_THREADS;
+    auto bail = [&](int e) {
+        release_staged(h, false);
+        in->busy = false;
+        delete h;
+        return e;
+    };
+    in->h_argv.assign(need, 0);
+    uint64_t *ptrs = (uint64_t *)in->h_argv.data();
+    size_t off = (size_t)(argc + 1) * 8;
+    for (int k = 0; k < argc; k++) {
+        const size_t n = strlen(argv[k]) + 1;
+        memcpy(in->h_argv.data() + off, argv[k], n);
+        ptrs[k] = (uint64_t)in->d_argv + off;
+        off += n;
+    }
+    ptrs[argc] = 0;
+    if (cudaMemcpyAsync(in->d_argv, in->h_argv.data(), need, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return bail(GF_ECUDA);
+    /* mapped buffers */
+    gf_state &s = in->h_init;
+    memset(&s, 0, sizeof s);
+    for (int k = 0; k < nbufs; k++) {
+        cudaPointerAttributes at;
+        void *dev = bufs[k].ptr;
+        bool owned = false;
+        if (bufs[k].ptr && bufs[k].bytes) {
+            if (cudaPointerGetAttributes(&at, bufs[k].ptr) != cudaSuccess)
+                return bail(GF_EINVAL);
+            if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) {
+                if (cudaMallocAsync(&dev, bufs[k].bytes, h->stream) != cudaSuccess)
+                    return bail(GF_ENOMEM);
+                owned = true;
+                h->staged.push_back({bufs[k].ptr, dev, bufs[k].bytes, bufs[k].dir, true});
+                if ((bufs[k].dir & GF_BUF_IN) &&
+                    cudaMemcpyAsync(dev, bufs[k].ptr, bufs[k].bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+                    return bail(GF_ECUDA);
+            }
+        }
+        (void)owned;
+        s.buf_ptr[k] = (uint64_t)dev;
+        s.buf_bytes[k] = bufs[k].bytes;
+    }
+    s.nbufs = (uint32_t)nbufs;
+    s.nblocks = grid;
+    s.block_dim = GF_BLOCK_THREADS;
+    s.nworkers = grid * GF_BLOCK_THREADS - 32;
+    s.aggregate = c->cfg.aggregate;
+    s.timeout_ns = c->cfg.timeout_ns;
+    s.ring_slots = c->ring_dev + (uint64_t)in->idx * c->cfg.ring_slots * c->cfg.slot_bytes;
+    s.nslots = c->cfg.ring_slots;
+    s.slot_bytes = c->cfg.slot_bytes;
+    s.fmt_cache = (uint64_t)in->d_fmt;
+    s.fmt_cache_cap = c->cfg.fmt_cache;
+    s.prog_id = (uint32_t)in->idx;
+    s.partials = (uint64_t)in->d_partials;
+    gf_heap &H = s.heap;
+    H.base = (uint64_t)in->d_heap;
+    H.bytes = in->slab_bytes + in->large_bytes;
+    H.slab_base = (uint64_t)in->d_heap;
+    H.slab_bytes = in->slab_bytes;
+    H.large_base = (uint64_t)in->d_heap + in->slab_bytes;
+    H.large_bytes = in->large_bytes;
+    H.slab_meta = (uint64_t)in->d_meta;
+    H.free_heads = (uint64_t)in->d_heads;
+    H.cur_slab = (uint64_t)in->d_cur;
+    H.large_ext = (uint64_t)in->d_ext;
+    H.large_size = (uint64_t)in->d_lsize;
+    H.nslabs = in->nslabs;
+    H.npages = in->npages;
+    H.large_next = in->npages ? 1 : 0;
+    in->h_ext0 = (uint64_t)0 | ((uint64_t)in->npages << 32);
+    if (cudaMemcpyAsync(in->d_state, &s, sizeof s, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(in->d_meta, 0, (size_t)std::max<uint32_t>(in->nslabs, 1) * 16, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(in->d_heads, 0, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 8, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(in->d_cur, 0, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 4, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(in->d_lsize, 0, (size_t)std::max<uint32_t>(in->npages, 1) * 4, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(in->d_fmt, 0, (size_t)c->cfg.fmt_cache * 8, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(in->d_ext, &in->h_ext0, 8, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return bail(GF_ECUDA);
+    /* ring segment: every slot free for its first ticket */
+    const uint32_t nthr = std::max<uint32_t>(1, c->cfg.server_threads);
+    for (uint32_t k = 0; k < in->seg.nslots; k++) {
+        gf_slot_hdr *hd = (gf_slot_hdr *)(in->seg.slots + (size_t)k * in->seg.slot_bytes);
+        __atomic_store_n(&hd->seq, (uint64_t)k, __ATOMIC_RELEASE);
+    }
+    in->seg.reset(nthr);
+    in->seg.active.store(true, std::memory_order_release);
+    c->nactive++;
+    c->act_cv.notify_all();
+    int a_argc = argc;
+    char **a_argv = (char **)in->d_argv;
+    gf_state *a_state = in->d_state;
+    void *args[3] = {&a_state, &a_argc, &a_argv};
+    cudaError_t le = pe.launch(args, grid, GF_BLOCK_THREADS, h->stream);
+    if (le != cudaSuccess || cudaEventRecord(in->ev_done, h->stream) != cudaSuccess) {
+        fprintf(stderr, "gf: launch of %s failed: %s\n", pe.name.c_str(), cudaGetErrorString(le));
+        in->seg.active = false;
+        c->nactive--;
+        return bail(GF_ECUDA);
+    }
+    *out = h;
+    return GF_OK;
+}
+
+extern "C" GF_API int gf_done(gf_handle *h)
+{
+    if (!h)
+        return 1;
+    return cudaEventQuery(h->inst->ev_done) == cudaErrorNotReady ? 0 : 1;
+}
+
+static double hist_pct(const uint64_t *hist, double q)
+{
+    uint64_t tot = 0;
+    for (int k = 0; k < GF_LAT_BUCKETS; k++)
+        tot += hist[k];
+    if (!tot)
+        return 0.0;
+    const double want = q * (double)tot;
+    uint64_t acc = 0;
+    for (int k = 0; k < GF_LAT_BUCKETS; k++) {
+        acc += hist[k];
+        if ((double)acc >= want) {
+            if (k < 8)
+                return (double)k;
+            const int e = k / 8, sub = k % 8;
+            /* bucket covers [2^e (1 + sub/8), 2^e (1 + (sub+1)/8)): report its midpoint */
+            return ldexp(1.0 + (sub + 0.5) / 8.0, e);
+        }
+    }
+    return 0.0;
+}
+
+extern "C" GF_API int gf_wait(gf_handle *h, int *exit_code, int64_t timeout_ns)
+{
+    if (!h)
+        return GF_EINVAL;
+    gf_ctx *c = h->ctx;
+    Instance *in = h->inst;
+    const auto t0 = std::chrono::steady_clock::now();
+    uint32_t spins = 0;
+    for (;;) {
+        cudaError_t q = cudaEventQuery(in->ev_done);
+        if (q == cudaSuccess)
+            break;
+        if (q != cudaErrorNotReady) {
+            fprintf(stderr, "gf: program failed: %s\n", cudaGetErrorString(q));
+            in->seg.active = false;
+            c->nactive--;
+            release_staged(h, false);
+            in->busy = false;
+            delete h;
+            return GF_ECUDA;
+        }
+        if (c->cfg.server_threads == 0)
+            c->server.poll(in->seg, 0, 1);
+        else if (++spins > 256)
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if (timeout_ns > 0 &&
+            std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count() >
+                timeout_ns)
+            return GF_ETIMEDOUT;
+    }
+    in->seg.active.store(false, std::memory_order_release);
+    c->nactive--;
+    int rc = GF_OK;
+    if (cudaMemcpyAsync(&in->h_final, in->d_state, sizeof(gf_state), cudaMemcpyDeviceToHost, h->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        rc = GF_ECUDA;
+    release_staged(h, true);
+    {
+        std::lock_guard<std::mutex> g(c->stats_mu);
+        gf_stats &st = c->last;
+        const gf_state &f = in->h_final;
+        memset(&st, 0, sizeof st);
+        for (int k = 0; k < GF_NOPS && k < GF_NSTAT; k++) {
+            st.rpc_calls[k] = f.st_calls[k];
+            st.rpc_slots[k] = f.st_slots[k];
+        }
+        st.rpc_wait_ns = f.st_wait_ns;
+        st.rpc_p50_ns = hist_pct(f.lat_hist, 0.50);
+        st.rpc_p99_ns = hist_pct(f.lat_hist, 0.99);
+        st.regions = f.st_regions;
+        st.heap_alloc = f.heap.n_alloc;
+        st.heap_free = f.heap.n_free;
+        st.heap_fail = f.heap.n_fail;
+        st.heap_bad_free = f.heap.n_bad_free;
+        st.heap_live_bytes = f.heap.live_bytes;
+        st.heap_high_water = f.heap.high_water;
+        st.main_ns = f.t_main_end > f.t_main_start ? f.t_main_end - f.t_main_start : 0;
+        st.host_slots = c->server.stats.slots;
+        st.host_records = c->server.stats.records;
+        st.host_ns = c->server.stats.ns;
+        st.host_dma_bytes = c->server.stats.dma_bytes;
+        st.grid = (int32_t)h->grid;
+        st.block = (int32_t)h->block;
+        st.error = f.error;
+        st.exit_code = f.exit_code;
+    }
+    if (rc == GF_OK && in->h_final.error)
+        rc = in->h_final.error;
+    if (exit_code)
+        *exit_code = in->h_final.exit_code;
+    if (c->out)
+        fflush(c->out);
+    in->busy = false;
+    delete h;
+    return rc;
+}
+
+extern "C" GF_API int gf_run_main(gf_ctx *c, gf_program prog, int argc, const char *const *argv, const gf_buf *bufs,
+                                  int nbufs, int *exit_code)
+{
+    gf_handle *h = nullptr;
+    int rc = gf_launch(c, prog, argc, argv, bufs, nbufs, nullptr, 0, &h);
+    if (rc)
+        return rc;
+    return gf_wait(h, exit_code, 0);
+}
+
+extern "C" GF_API int gf_rpc_serve(gf_ctx *c, const gf_serve_opts *o)
+{
+    if (!c)
+        return GF_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        if (o && o->stop && *o->stop)
+            return GF_OK;
+        bool any = false;
+        for (Instance *in : c->inst)
+            if (in->seg.active.load(std::memory_order_acquire)) {
+                if (c->cfg.server_threads == 0)
+                    c->server.poll(in->seg, 0, 1);
+                if (cudaEventQuery(in->ev_done) == cudaErrorNotReady)
+                    any = true;   /* finished programs are collected by gf_wait */
+            }
+        if (!any)
+            return GF_OK;
+        if (o && o->timeout_ns > 0 &&
+            std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count() >
+                o->timeout_ns)
+            return GF_ETIMEDOUT;
+        if (c->cfg.server_threads)
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+extern "C" GF_API int gf_get_stats(gf_ctx *c, gf_stats *out)
+{
+    if (!c || !out)
+        return GF_EINVAL;
+    std::lock_guard<std::mutex> g(c->stats_mu);
+    *out = c->last;
+    return GF_OK;
+}

@@ -1,0 +1,56 @@
+"""The C-ABI library loads without a GPU and exports every function that
+include/gf.h declares with GF_API (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"GF_API\s+[\w\s\*]+?\b(gf_\w+)\s*\(", src)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as ge
+    ge.build()
+    return ctypes.CDLL(os.path.join(ROOT, "paper_2306_11686_gb300", "libgf.so"))
+
+
+def test_header_declares_the_boundary():
+    names = set(declared())
+    for n in ["gf_init", "gf_finalize", "gf_run_main", "gf_launch", "gf_wait", "gf_rpc_serve",
+              "gf_rpc_register", "gf_get_stats", "gf_strerror", "gf_program_lookup"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_defaults_without_gpu(lib):
+    from paper_2306_11686_gb300 import gf
+    assert gf.gf_strerror(gf.GF_ETIMEDOUT).decode().startswith("timed out")
+    c = gf.gf_config()
+    gf.gf_config_default(ctypes.byref(c))
+    assert c.ring_slots == 4096 and c.aggregate == 1 and c.max_programs == 1
+    bad = gf.gf_config()
+    gf.gf_config_default(ctypes.byref(bad))
+    bad.ring_slots = 1000                                   # not a power of two
+    h = ctypes.c_void_p()
+    assert gf.gf_init(ctypes.byref(bad), ctypes.byref(h)) == gf.GF_EINVAL
+
+
+def test_programs_registered(lib):
+    from paper_2306_11686_gb300 import gf
+    # lookup needs a context; the registry itself is visible through the symbol table instead
+    assert hasattr(lib, "gf_program_register")

@@ -1,0 +1,107 @@
+"""Parity of the GPU path against the serial C oracle, through the C ABI.
+
+Bar (written here, per kind of result):
+- printf text, written files, integer/index results: bit-exact;
+- elementwise FP64 (axpy y, Jacobi grid, residuals): bit-exact, since both
+  sides evaluate the same expression with no contraction (oracle built with
+  -ffp-contract=off, device code with --fmad=false) and IEEE division;
+- FP64 sums: |gpu - oracle| <= 1e-12 |oracle|, and |gpu - exact| <= 2 eps sum|y|
+  against the exactly rounded sum.
+stdout is compared as a multiset of lines (OpenMP leaves the interleaving of
+output from different threads unspecified).
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2306_11686_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+EPS = 2.0 ** -52
+
+
+def oracle(oracle_bin, name, *args):
+    p = subprocess.run([oracle_bin(name), *map(str, args)], capture_output=True, text=True)
+    assert p.returncode == 0, p.stderr
+    return p.stdout
+
+
+def split_sum(lines):
+    body = sorted(l for l in lines if not l.startswith("sum "))
+    s = [float(l.split()[1]) for l in lines if l.startswith("sum ")]
+    return body, s
+
+
+@pytest.mark.parametrize("n", [0, 1, 1023, 1025, 5000 + 17, 1 << 20])
+def test_axpy_sum_parity(gf_lib, oracle_bin, tmp_path, n):
+    import torch
+    gf = gf_lib
+    x, y = inputs.axpy_inputs(n, seed=1)
+    inputs.write_f64(tmp_path / "x.bin", x)
+    inputs.write_f64(tmp_path / "y.bin", y)
+    want = oracle(oracle_bin, "axpy_sum", n, tmp_path / "x.bin", tmp_path / "y.bin", tmp_path / "ref.bin")
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20) as ctx:
+        rc, ec = ctx.run("axpy_sum", [n, tmp_path / "gpu.bin"], [(xd, gf.GF_BUF_IN), (yd, gf.GF_BUF_IN)])
+        st = ctx.stats()
+    assert ec == 0
+    got = open(tmp_path / "out.txt").read().splitlines()
+    gb, gs = split_sum(got)
+    wb, ws = split_sum(want.splitlines())
+    assert gb == wb
+    assert len(gs) == 1 and len(ws) == 1
+    assert abs(gs[0] - ws[0]) <= 1e-12 * abs(ws[0])
+    ex = dict(l.split() for l in oracle(oracle_bin, "exact_sum", tmp_path / "ref.bin").splitlines())
+    assert abs(gs[0] - float(ex["exact"])) <= 2 * EPS * float(ex["absum"])
+    assert (tmp_path / "gpu.bin").read_bytes() == (tmp_path / "ref.bin").read_bytes()
+    assert st.rpc_calls[gf.OP_PRINTF] == (n + 1023) // 1024 + 1
+    assert st.regions == (2 if n else 0)
+
+
+def test_axpy_closed_form_sum_is_exact(gf_lib, tmp_path):
+    import torch
+    gf = gf_lib
+    n = 1 << 20
+    x, y = inputs.axpy_closed_form_inputs(n)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20) as ctx:
+        ctx.run("axpy_sum", [n, tmp_path / "gpu.bin"], [(xd, gf.GF_BUF_IN), (yd, gf.GF_BUF_IN)])
+    s = [l for l in open(tmp_path / "out.txt").read().splitlines() if l.startswith("sum ")]
+    assert s == ["sum %.17g" % (2.5 * n * (n - 1) / 2 + n)]
+
+
+def test_axpy_host_buffers_e2e(gf_lib, oracle_bin, tmp_path):
+    """Host (numpy) buffers: the loader stages them in and out."""
+    gf = gf_lib
+    n = 70000
+    x, y = inputs.axpy_inputs(n, seed=3)
+    inputs.write_f64(tmp_path / "x.bin", x)
+    inputs.write_f64(tmp_path / "y.bin", y)
+    oracle(oracle_bin, "axpy_sum", n, tmp_path / "x.bin", tmp_path / "y.bin", tmp_path / "ref.bin")
+    yh = y.copy()
+    with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20) as ctx:
+        rc, ec = ctx.run("axpy_sum", [n, tmp_path / "gpu.bin"], [(x, gf.GF_BUF_IN), (yh, gf.GF_BUF_IN | gf.GF_BUF_OUT)])
+    assert ec == 0
+    assert np.array_equal(yh, np.fromfile(tmp_path / "ref.bin"))
+
+
+@pytest.mark.parametrize("n,sweeps", [(3, 2), (8, 3), (18, 4), (67, 5), (256, 100)])
+def test_jacobi_parity(gf_lib, oracle_bin, tmp_path, n, sweeps):
+    import torch
+    gf = gf_lib
+    g = inputs.jacobi_input(n, seed=2)
+    inputs.write_f64(tmp_path / "in.bin", g)
+    want = oracle(oracle_bin, "jacobi", n, sweeps, tmp_path / "in.bin", tmp_path / "ref.bin")
+    gd = torch.from_numpy(g).cuda()
+    heap = max(64 << 20, 4 * n ** 3 * 8 + (64 << 20))
+    with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=heap, heap_small_pct=5) as ctx:
+        rc, ec = ctx.run("jacobi", [n, sweeps, tmp_path / "gpu.bin"], [(gd, gf.GF_BUF_IN)])
+        st = ctx.stats()
+    assert ec == 0
+    got = open(tmp_path / "out.txt").read().splitlines()
+    assert sorted(got) == sorted(want.splitlines())          # residual text bit-exact
+    assert (tmp_path / "gpu.bin").read_bytes() == (tmp_path / "ref.bin").read_bytes()
+    assert st.heap_alloc == sweeps and st.heap_free == sweeps and st.heap_bad_free == 0
+    assert st.heap_live_bytes == 0

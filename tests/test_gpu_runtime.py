@@ -1,0 +1,227 @@
+"""GPU tests of the runtime mechanisms, each against brute force or a closed
+form: schedules (every iteration exactly once, OpenMP static assignment),
+reductions, the cross-block barrier, RPC landing pads, warp aggregation, the
+heap audit (pairwise non-overlap, alignment, bounds) and bounded waits."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2306_11686_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(gf_lib, tmp_path_factory):
+    d = tmp_path_factory.mktemp("rt")
+    c = gf_lib.Context(timeout_ns=10_000_000_000, stdout_path=d / "out.txt", heap_bytes=1 << 30)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("b,e,sched,chunk", [
+    (0, 1, 0, 1), (0, 1000, 0, 1), (5, 300017, 0, 1), (0, 300017, 0, 0), (3, 100000, 0, 7),
+    (0, 777777, 1, 1), (11, 500000, 1, 13), (0, 31, 1, 64), (0, 0, 0, 1)])
+def test_schedules(gf_lib, ctx, b, e, sched, chunk):
+    import torch
+    gf = gf_lib
+    n = e - b
+    hits = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+    owner = torch.full((max(n, 1),), -1, dtype=torch.int64, device="cuda")
+    info = torch.zeros(2, dtype=torch.int64, device="cuda")
+    rc, ec = ctx.run("sched_probe", [b, e, sched, chunk], [(hits, 1), (owner, 1), (info, 1)])
+    assert ec == 0
+    if n == 0:
+        assert info[0].item() == 0
+        return
+    T = info[0].item()
+    sms, per = ctx.grid_info("sched_probe")
+    assert T == sms * per * 256 - 32                       # every SM, continuous ids
+    assert info[1].item() == 1                              # serial part: a team of one
+    assert torch.all(hits[:n] == 1)                         # each iteration exactly once
+    o = owner[:n].cpu().numpy()
+    i = np.arange(n)
+    if sched == 0 and chunk == 1:
+        assert np.array_equal(o, i % T)
+    elif sched == 0 and chunk > 1:
+        assert np.array_equal(o, (i // chunk) % T)
+    elif sched == 0:
+        per_t = -(-n // T)
+        assert np.array_equal(o, i // per_t)
+    else:
+        assert o.min() >= 0 and o.max() < T
+
+
+@pytest.mark.parametrize("n,sched,chunk", [(1, 0, 1), (1000, 0, 1), (1 << 20, 0, 1), (123457, 1, 5), (99, 0, 0)])
+def test_reductions(gf_lib, ctx, n, sched, chunk):
+    import torch
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) * 10.0 ** rng.integers(-8, 8, n)
+    v = rng.integers(-2 ** 40, 2 ** 40, n)
+    out = torch.zeros(6, dtype=torch.int64, device="cuda")
+    ctx.run("reduce_probe", [n, sched, chunk],
+            [(torch.from_numpy(x).cuda(), 1), (torch.from_numpy(v).cuda(), 1), (out, 1)])
+    o = out.cpu().numpy()
+    d = o[:3].view(np.float64)
+    exact = math.fsum(x)
+    assert abs(d[0] - exact) <= 2 * 2.0 ** -52 * np.abs(x).sum()
+    assert d[1] == x.min() and d[2] == x.max()
+    assert o[3] == int(v.sum()) and o[4] == v.min() and o[5] == v.max()
+
+
+def test_reduction_deterministic(gf_lib, ctx):
+    import torch
+    n = 1 << 19
+    x = inputs.uniform_pm1(9, n) * 1e6
+    xd = torch.from_numpy(x).cuda()
+    vd = torch.zeros(n, dtype=torch.int64, device="cuda")
+    res = set()
+    for _ in range(3):
+        out = torch.zeros(6, dtype=torch.int64, device="cuda")
+        ctx.run("reduce_probe", [n, 1, 3], [(xd, 1), (vd, 1), (out, 1)])
+        res.add(out[0].item())
+    assert len(res) == 1
+
+
+def test_grid_barrier(gf_lib, ctx):
+    import torch
+    sms, per = ctx.grid_info("barrier_probe")
+    T = sms * per * 256 - 32
+    a = torch.zeros(T, dtype=torch.int64, device="cuda")
+    err = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rc, ec = ctx.run("barrier_probe", [20], [(a, 1), (err, 1)])
+    assert ec == 0 and err.item() == 0
+
+
+def test_rpc_landing_pads(gf_lib, tmp_path):
+    import torch
+    gf = gf_lib
+    os.environ["GF_PROBE_VAR"] = "value-42"
+    os.environ.pop("GF_PROBE_UNSET_VAR", None)
+    nbig = (3 << 20) + 123
+    big = torch.from_numpy(np.frombuffer(np.random.default_rng(1).bytes(nbig), dtype=np.uint8).copy()).cuda()
+    ref = big.clone()
+    res = torch.zeros(32, dtype=torch.int64, device="cuda")
+    with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20) as c:
+        rc, ec = c.run("rpc_probe", [tmp_path / "small.txt", tmp_path / "big.bin", nbig], [(res, 1), (big, 1)])
+    assert ec == 0
+    lines = open(tmp_path / "out.txt").read().splitlines()
+    want = [
+        "int %d %i %u %x %X %o|" % (-42, 7, 4000000000, 255, 3054, 8),
+        "long %d %d %d %x" % (-5000000000, 123456789012345, 18446744073709551615, 0xdeadbeefcafe),
+        "dbl %f %e %g %.17g %10.3f|%-8.2e|%+.0f" % (3.14159, -1.5e-300, 1e100, 0.1, 2.5, 12345.678, 2.5),
+        "str [%s] [%10s] [%-6s] [%.3s] %c%c %%" % ("hello", "right", "left", "truncate", "o", "k"),
+        "star [%*d] [%-*d] [%.*f]" % (6, 42, 5, 7, 3, 1.0 / 3.0),
+        "no args",
+    ]
+    assert lines == want
+    r = res.cpu().tolist()
+    assert r[:6] == [len(w) + 1 for w in want]
+    assert r[6] == 1 and r[7] == len("to file 99 ok\n") and r[8] == 16 and r[9] == 0
+    assert open(tmp_path / "small.txt").read() == "to file 99 ok\n0123456789abcdef"
+    assert r[10] == nbig and r[11] == 0
+    assert (tmp_path / "big.bin").read_bytes() == ref.cpu().numpy().tobytes()
+    assert r[12] == 20
+    h = 0
+    for ch in b"to file 99 ok\n012345":
+        h = (h * 31 + ch) & ((1 << 64) - 1)
+    assert r[13] == (h if h < 1 << 63 else h - (1 << 64))
+    assert r[14] == nbig and torch.equal(big, ref)           # fread by DMA restored the bytes
+    assert r[15] == len("value-42") and r[16] == ord("v") and r[17] == 0
+    assert r[18] == 1 and r[19] == 1
+
+
+@pytest.mark.parametrize("aggregate", [1, 0])
+def test_rpc_storm_order_and_multiset(gf_lib, tmp_path, aggregate):
+    import torch
+    gf = gf_lib
+    n, calls = 20000, 4
+    bad = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20, aggregate=aggregate) as c:
+        rc, ec = c.run("rpc_storm", [n, calls], [(bad, 1)])
+        st = c.stats()
+    assert ec == 0 and bad.item() == 0
+    lines = open(tmp_path / "out.txt").read().splitlines()
+    want = ["t %d k %d v %.6e" % (i, k, i * 0.5 + k) for i in range(n) for k in range(calls)]
+    assert sorted(lines) == sorted(want)
+    last = {}
+    for l in lines:                                          # per-thread program order
+        p = l.split()
+        i, k = int(p[1]), int(p[3])
+        assert last.get(i, -1) == k - 1
+        last[i] = k
+    assert st.rpc_calls[gf.OP_PRINTF] == n * calls
+    if aggregate:
+        assert st.rpc_slots[gf.OP_PRINTF] < st.rpc_calls[gf.OP_PRINTF] / 8
+    else:
+        assert st.rpc_slots[gf.OP_PRINTF] == st.rpc_calls[gf.OP_PRINTF]
+
+
+def test_heap_audit(gf_lib, tmp_path):
+    import torch
+    gf = gf_lib
+    n, per = 4096, 8
+    sizes = inputs.loguniform_int(11, n * per, 16, 65536).astype(np.uint32)
+    ptrs = torch.zeros(n * per, dtype=torch.int64, device="cuda")
+    info = torch.zeros(4, dtype=torch.int64, device="cuda")
+    with gf.Context(timeout_ns=10_000_000_000, heap_bytes=2 << 30, heap_small_pct=90) as c:
+        rc, ec = c.run("heap_audit", [n, per], [(torch.from_numpy(sizes.view(np.int32)).cuda(), 1), (ptrs, 1), (info, 1)])
+        st = c.stats()
+        hb = c.cfg.heap_bytes
+    assert ec == 0
+    p = ptrs.cpu().numpy().view(np.uint64)
+    assert (p != 0).all()
+    cls = np.maximum(16, 1 << np.ceil(np.log2(sizes)).astype(np.int64))
+    order = np.argsort(p)
+    ps, cs = p[order].astype(np.int64), cls[order]
+    assert (ps % 16 == 0).all()
+    assert (ps[1:] >= ps[:-1] + cs[:-1]).all()               # pairwise non-overlap
+    assert ps[-1] + cs[-1] - ps[0] <= hb                     # inside the arena
+    inf = info.cpu().tolist()
+    assert inf[0] == 0                                       # every block kept its tags
+    assert inf[1] == int(cls.sum()) and inf[2] == 0          # live bytes, then all freed
+    assert inf[3] == n * per                                 # reuse succeeds
+    assert st.heap_fail == 0 and st.heap_bad_free == 0
+
+
+def test_heap_large_path(gf_lib):
+    import torch
+    gf = gf_lib
+    out = torch.zeros(16, dtype=torch.int64, device="cuda")
+    with gf.Context(timeout_ns=10_000_000_000, heap_bytes=1 << 30, heap_small_pct=0) as c:
+        rc, ec = c.run("heap_big", [100 << 20, 4], [(out, 1)])
+        st = c.stats()
+    o = out.cpu().numpy().view(np.uint64)
+    assert ec == 0
+    assert len(set(o[:4].tolist())) == 4 and (o[:4] != 0).all()
+    assert o[4] == o[1]                                      # first fit reuses the hole
+    assert o[5] == o[0]                                      # all extents merged back
+    assert st.heap_bad_free == 1 and st.heap_live_bytes == 0
+
+
+def test_heap_out_of_memory_returns_null(gf_lib):
+    import torch
+    gf = gf_lib
+    out = torch.zeros(16, dtype=torch.int64, device="cuda")
+    with gf.Context(timeout_ns=10_000_000_000, heap_bytes=256 << 20, heap_small_pct=0) as c:
+        rc, ec = c.run("heap_big", [100 << 20, 4], [(out, 1)])
+        st = c.stats()
+    o = out.cpu().numpy()
+    assert o[0] != 0 and o[1] != 0 and o[2] == 0 and o[3] == 0   # only two 100 MiB blocks fit
+    assert st.heap_fail >= 2
+
+
+def test_rpc_timeout_without_server(gf_lib):
+    gf = gf_lib
+    with gf.Context(server_threads=0, timeout_ns=200_000_000, heap_bytes=64 << 20) as c:
+        rc, h = c.launch("rpc_timeout", [])
+        assert rc == 0
+        import time
+        t0 = time.time()
+        while not gf.gf_done(h):
+            assert time.time() - t0 < 30
+            time.sleep(0.01)
+        rc, ec = c.wait(h)
+    assert ec == 1 and rc == gf.GF_ETIMEDOUT
