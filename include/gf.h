@@ -91,6 +91,7 @@ typedef struct gf_stats {
     double rpc_p50_ns;            /* device round-trip latency percentiles (claim -> done) */
     double rpc_p99_ns;
     uint64_t regions;             /* parallel regions run                                   */
+    uint64_t region_ns;           /* device time inside regions (publish -> all blocks done) */
     uint64_t heap_alloc, heap_free, heap_fail, heap_bad_free;
     uint64_t heap_live_bytes, heap_high_water;
     uint64_t main_ns;             /* device time from main() entry to return               */

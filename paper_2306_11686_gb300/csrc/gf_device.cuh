@@ -204,23 +204,35 @@ template <> struct acc<double, GF_RED_SUM> {
     }
 };
 
+/* double min / max on the integer pipe: flipping the magnitude bits of
+ * negative values makes the signed 64-bit order of the bit patterns equal to
+ * the IEEE order (with -0 < +0), so no FP64 instruction is spent per element
+ * (GB300 issues FP64 at a small fraction of its integer rate).  NaNs are
+ * skipped, as `if (x > m) m = x` skips them.  Between -0 and +0 max returns
+ * +0 and min returns -0, either of which the unordered reduction allows. */
+__device__ __forceinline__ long long f64_key(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
 template <int OP> struct acc<double, OP> {
-    double v;
-    __device__ acc() : v(OP == GF_RED_MIN ? __builtin_huge_val()
-                                          : -__builtin_huge_val()) {}
+    long long k;
+    __device__ acc() : k(OP == GF_RED_MIN ? 0x7ff0000000000000ll : (long long)0x800fffffffffffffull) {}
+    __device__ void add_key(long long x) { k = OP == GF_RED_MIN ? (x < k ? x : k) : (x > k ? x : k); }
     __device__ void add(double x)
     {
-        if (OP == GF_RED_MIN ? (x < v) : (x > v))
-            v = x;
+        const long long b = __double_as_longlong(x);
+        if ((b & 0x7fffffffffffffffll) <= 0x7ff0000000000000ll)      /* not a NaN */
+            add_key(b ^ ((b >> 63) & 0x7fffffffffffffffll));
     }
-    __device__ void merge(const acc &o) { add(o.v); }
-    __device__ double result() const { return v; }
-    __device__ void to_words(uint64_t *w) const { w[0] = __double_as_longlong(v); w[1] = 0; }
-    __device__ void from_words(const uint64_t *w) { v = __longlong_as_double(w[0]); }
+    __device__ void merge(const acc &o) { add_key(o.k); }
+    __device__ double result() const { return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll)); }
+    __device__ void to_words(uint64_t *w) const { w[0] = (uint64_t)k; w[1] = 0; }
+    __device__ void from_words(const uint64_t *w) { k = (long long)w[0]; }
     __device__ acc shfl_xor(int m) const
     {
         acc r;
-        r.v = __shfl_xor_sync(0xffffffffu, v, m);
+        r.k = __shfl_xor_sync(0xffffffffu, k, m);
         return r;
     }
 };
@@ -372,6 +384,7 @@ static __device__ __noinline__ int run_region(gf_state *S)
     S->done_target = target;
     S->dyn_next = 0;
     S->red_ticket = 0;
+    const uint64_t t0 = now_ns();
     __threadfence();
     st_rel_gpu(&S->epoch, S->epoch + 1);
     backoff bo(S->timeout_ns);
@@ -381,6 +394,7 @@ static __device__ __noinline__ int run_region(gf_state *S)
             return GF_ETIMEDOUT;
         }
     }
+    S->st_region_ns += now_ns() - t0;
     return GF_OK;
 }
 

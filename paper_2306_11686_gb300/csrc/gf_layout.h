@@ -172,6 +172,7 @@ typedef struct gf_state {
     uint64_t st_slots[GF_NSTAT];  /* ring slots per opcode                            */
     uint64_t st_wait_ns;          /* device ns spent waiting for the host             */
     uint64_t st_regions;
+    uint64_t st_region_ns;        /* initial thread: publish -> all blocks done       */
     uint64_t t_main_start, t_main_end;
     uint64_t lat_hist[GF_LAT_BUCKETS];  /* RPC round trips (claim -> host done), lane records */
     gf_heap heap;

@@ -1,9 +1,11 @@
 /* Host RPC server: slot scanning and the libc landing pads (see server.h). */
 #include "server.h"
 
+#include <fcntl.h>
 #include <stdlib.h>
 #include <string.h>
 #include <time.h>
+#include <unistd.h>
 #include <chrono>
 #include <vector>
 
@@ -328,7 +330,34 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec)
         if (op == GF_OP_FWRITE) {
             if (!d2h_)
                 return 0;
-            done = d2h_(dev, bytes, [&](const void *c, uint64_t n) { return fwrite(c, 1, n, f) == n; });
+            /* A seekable file not opened for append takes the chunks with
+             * pwrite at their offsets from several threads (page-cache copies
+             * scale with threads); the stdio position is moved past the data
+             * afterwards.  Anything else gets the chunks in order via fwrite. */
+            fflush(f);
+            const int fd = fileno(f);
+            const off_t base = ftello(f);
+            const int fl = fd >= 0 ? fcntl(fd, F_GETFL) : -1;
+            const bool par = base >= 0 && fl >= 0 && !(fl & O_APPEND) && lseek(fd, 0, SEEK_CUR) == base;
+            if (par) {
+                done = d2h_(dev, bytes,
+                            [&](const void *c, uint64_t n, uint64_t pos) {
+                                const uint8_t *p = (const uint8_t *)c;
+                                uint64_t w = 0;
+                                while (w < n) {
+                                    const ssize_t k = pwrite(fd, p + w, n - w, base + (off_t)(pos + w));
+                                    if (k <= 0)
+                                        return false;
+                                    w += (uint64_t)k;
+                                }
+                                return true;
+                            },
+                            true);
+                fseeko(f, base + (off_t)done, SEEK_SET);
+            } else {
+                done = d2h_(dev, bytes, [&](const void *c, uint64_t n, uint64_t) { return fwrite(c, 1, n, f) == n; },
+                            false);
+            }
         } else {
             if (!h2d_)
                 return 0;

@@ -46,10 +46,13 @@ struct Segment {
     void reset(uint32_t nthreads);
 };
 
-/* Streams a device range to `sink` chunk by chunk (fwrite DMA); returns the
- * bytes the sink accepted.  The sink returns false to stop. */
-typedef std::function<bool(const void *chunk, uint64_t n)> sink_fn;
-typedef std::function<uint64_t(uint64_t dev_src, uint64_t bytes, const sink_fn &sink)> d2h_fn;
+/* Streams a device range to `sink` chunk by chunk (fwrite DMA); `pos` is the
+ * chunk's offset in the range.  With parallel = false chunks arrive in order
+ * from one thread; with parallel = true they may arrive from several threads
+ * at once and out of order (the sink writes at pos).  Returns the length of
+ * the prefix the sink accepted; the sink returns false to stop. */
+typedef std::function<bool(const void *chunk, uint64_t n, uint64_t pos)> sink_fn;
+typedef std::function<uint64_t(uint64_t dev_src, uint64_t bytes, const sink_fn &sink, bool parallel)> d2h_fn;
 /* Fills a device range from `source` chunk by chunk (fread DMA); the source
  * returns how many bytes it produced (fewer ends the transfer). */
 typedef std::function<uint64_t(void *buf, uint64_t want)> source_fn;

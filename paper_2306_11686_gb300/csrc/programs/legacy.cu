@@ -7,6 +7,7 @@
  * plain C with the real libc is what a run must reproduce.
  */
 #include "../gf_device.cuh"
+#include "../gf_fastdiv.cuh"
 
 /*
  * axpy_sum N out_path            buffers: 0 = x (N doubles), 1 = y (N doubles, updated)
@@ -89,7 +90,7 @@ GF_MAIN(jacobi)(int argc, char **argv)
                 v = v + u[c + nn];
                 v = v + u[c - sk];
                 v = v + u[c + sk];
-                v = v / 6.0;
+                v = gf_div6_rn(v);            /* == v / 6.0, bit for bit */
                 un[c] = v;
                 return fabs(v - u[c]);
             },

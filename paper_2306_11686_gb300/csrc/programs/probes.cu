@@ -4,6 +4,7 @@
  * audit and the bounded-wait error path.
  */
 #include "../gf_device.cuh"
+#include "../gf_fastdiv.cuh"
 
 /* sched_probe b e sched chunk      buffers: 0 = int32 hits[e-b], 1 = int64 owner[e-b], 2 = int64 info[2]
  * Every iteration records which continuous thread id ran it. */
@@ -247,4 +248,34 @@ GF_MAIN(rpc_timeout)(int argc, char **argv)
     int st = 0;
     gfd::rpc(GF_OP_CLOCK, nullptr, &st);
     return st == GF_ETIMEDOUT ? 1 : (st == GF_OK ? 0 : 2);
+}
+
+/* div6_probe n                     buffers: 0 = double x[n], 1 = double out[2n]: (x / 6.0, gf_div6_rn(x)) */
+GF_MAIN(div6_probe)(int argc, char **argv)
+{
+    const long long n = gf_atoll(argv[1]);
+    const double *x = (const double *)gf_buffer(0);
+    double *out = (double *)gf_buffer(1);
+    return gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) {
+        const double v = x[i];
+        out[2 * i] = v / 6.0;
+        out[2 * i + 1] = gf_div6_rn(v);
+    }) ? 10 : 0;
+}
+
+/* fwrite_modes path nbytes          buffer 0 = bytes; appends the buffer twice ("ab": in-order path),
+ * then writes it once more at offset 0 of a fresh file ("wb": parallel path) followed by a small tail */
+GF_MAIN(fwrite_modes)(int argc, char **argv)
+{
+    if (argc < 3)
+        return 2;
+    const unsigned char *b = (const unsigned char *)gf_buffer(0);
+    const long long n = gf_atoll(argv[2]);
+    GF_FILE f = gf_fopen(argv[1], "ab");
+    if (!f)
+        return 3;
+    long long w = (long long)gf_fwrite(b, 1, (size_t)n, f);
+    w += (long long)gf_fwrite(b, 1, (size_t)n, f);
+    gf_fclose(f);
+    return w == 2 * n ? 0 : 4;
 }

@@ -37,6 +37,7 @@
 #define GF_MAX_BLOCKS_PER_SM 32
 #define GF_ARGV_BYTES (64u * 1024u)
 #define GF_DMA_CHUNK (16ull << 20)
+#define GF_DMA_NSTAGE 8            /* pinned staging buffers of GF_DMA_CHUNK bytes */
 #define GF_INTERN_BYTES (1u << 20)
 #define GF_BLOCK_THREADS 256
 
@@ -116,8 +117,8 @@ struct gf_ctx {
     std::mutex act_mu;
     std::condition_variable act_cv;
     cudaStream_t own_stream = nullptr, dma_stream = nullptr;
-    void *dma_stage[2] = {nullptr, nullptr};
-    cudaEvent_t dma_ev[2] = {nullptr, nullptr};
+    void *dma_stage[GF_DMA_NSTAGE] = {};
+    cudaEvent_t dma_ev[GF_DMA_NSTAGE] = {};
     std::mutex dma_mu;
     uint8_t *intern_host = nullptr;
     uint64_t intern_dev = 0;
@@ -182,38 +183,73 @@ extern "C" GF_API const char *gf_strerror(int e)
 static bool pow2(uint64_t x) { return x && !(x & (x - 1)); }
 
 /* ------------------------------------------------------------------ DMA */
-static uint64_t dma_d2h(gf_ctx *c, uint64_t dev, uint64_t bytes, const gfh::sink_fn &sink)
+/*
+ * Device -> host streaming through the pinned staging buffers.  Chunk k goes
+ * to buffer k % nbuf; a buffer is refilled only after the sink has consumed
+ * its previous chunk.  Sequential mode double-buffers one copy against one
+ * sink call; parallel mode hands each landed chunk to its own writer thread
+ * so up to GF_DMA_NSTAGE sink calls run at once.
+ */
+static uint64_t dma_d2h(gf_ctx *c, uint64_t dev, uint64_t bytes, const gfh::sink_fn &sink, bool parallel)
 {
     std::lock_guard<std::mutex> g(c->dma_mu);
-    uint64_t pend[2] = {0, 0}, off = 0, delivered = 0;
-    int b = 0;
-    auto issue = [&](int k) {
-        const uint64_t n = std::min<uint64_t>(GF_DMA_CHUNK, bytes - off);
-        pend[k] = 0;
-        if (!n)
-            return true;
+    const int nbuf = parallel ? GF_DMA_NSTAGE : 2;
+    const uint64_t nchunk = (bytes + GF_DMA_CHUNK - 1) / GF_DMA_CHUNK;
+    std::vector<std::thread> writer(nbuf);
+    std::vector<int> ok(nchunk, 0);
+    std::vector<uint64_t> pend(nbuf, UINT64_MAX);   /* chunk held by each buffer in sequential mode */
+    bool failed = false;
+    auto consume_seq = [&](int k) {
+        if (pend[k] == UINT64_MAX)
+            return;
+        const uint64_t ch = pend[k], off = ch * GF_DMA_CHUNK, n = std::min<uint64_t>(GF_DMA_CHUNK, bytes - off);
+        ok[ch] = !failed && cudaEventSynchronize(c->dma_ev[k]) == cudaSuccess && sink(c->dma_stage[k], n, off);
+        failed |= !ok[ch];
+        pend[k] = UINT64_MAX;
+    };
+    for (uint64_t ch = 0; ch < nchunk && !failed; ch++) {
+        const int k = (int)(ch % nbuf);
+        const uint64_t off = ch * GF_DMA_CHUNK, n = std::min<uint64_t>(GF_DMA_CHUNK, bytes - off);
+        if (parallel) {
+            if (writer[k].joinable())
+                writer[k].join();
+        } else {
+            consume_seq(k);
+        }
         if (cudaMemcpyAsync(c->dma_stage[k], (const void *)(dev + off), n, cudaMemcpyDeviceToHost, c->dma_stream) !=
                 cudaSuccess ||
-            cudaEventRecord(c->dma_ev[k], c->dma_stream) != cudaSuccess)
-            return false;
-        pend[k] = n;
-        off += n;
-        return true;
-    };
-    if (!issue(0))
-        return 0;
-    while (pend[b]) {
-        if (!issue(1 - b))
+            cudaEventRecord(c->dma_ev[k], c->dma_stream) != cudaSuccess) {
+            failed = true;
             break;
-        if (cudaEventSynchronize(c->dma_ev[b]) != cudaSuccess)
-            break;
-        if (!sink(c->dma_stage[b], pend[b]))
-            break;
-        delivered += pend[b];
-        pend[b] = 0;
-        b = 1 - b;
+        }
+        if (parallel) {
+            writer[k] = std::thread([&, k, ch, off, n] {
+                ok[ch] = cudaEventSynchronize(c->dma_ev[k]) == cudaSuccess && sink(c->dma_stage[k], n, off);
+            });
+        } else {
+            pend[k] = ch;
+            consume_seq(1 - k);   /* the other buffer's chunk landed while this copy was issued */
+        }
+    }
+    if (parallel) {
+        for (auto &t : writer)
+            if (t.joinable())
+                t.join();
+    } else {
+        /* drain in chunk order */
+        for (int round = 0; round < 2; round++) {
+            int best = -1;
+            for (int k = 0; k < nbuf; k++)
+                if (pend[k] != UINT64_MAX && (best < 0 || pend[k] < pend[best]))
+                    best = k;
+            if (best >= 0)
+                consume_seq(best);
+        }
     }
     cudaStreamSynchronize(c->dma_stream);
+    uint64_t delivered = 0;
+    for (uint64_t ch = 0; ch < nchunk && ok[ch]; ch++)
+        delivered += std::min<uint64_t>(GF_DMA_CHUNK, bytes - ch * GF_DMA_CHUNK);
     return delivered;
 }
 
@@ -336,7 +372,7 @@ extern "C" GF_API int gf_finalize(gf_ctx *c)
         cudaFreeHost(c->ring_host);
     if (c->intern_host)
         cudaFreeHost(c->intern_host);
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < GF_DMA_NSTAGE; k++) {
         if (c->dma_stage[k])
             cudaFreeHost(c->dma_stage[k]);
         if (c->dma_ev[k])
@@ -400,7 +436,7 @@ extern "C" GF_API int gf_init(const gf_config *cfg, gf_ctx **out)
     void *idv = nullptr;
     cudaHostGetDevicePointer(&idv, c->intern_host, 0);
     c->intern_dev = (uint64_t)idv;
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < GF_DMA_NSTAGE; k++) {
         if (cudaHostAlloc(&c->dma_stage[k], GF_DMA_CHUNK, cudaHostAllocPortable) != cudaSuccess)
             return fail(GF_ENOMEM);
         if (cudaEventCreateWithFlags(&c->dma_ev[k], cudaEventDisableTiming) != cudaSuccess)
@@ -424,7 +460,7 @@ extern "C" GF_API int gf_init(const gf_config *cfg, gf_ctx **out)
         c->own_out = true;
     }
     c->server.set_stdout(c->out);
-    c->server.set_dma([c](uint64_t d, uint64_t n, const gfh::sink_fn &s) { return dma_d2h(c, d, n, s); },
+    c->server.set_dma([c](uint64_t d, uint64_t n, const gfh::sink_fn &s, bool par) { return dma_d2h(c, d, n, s, par); },
                       [c](uint64_t d, uint64_t n, const gfh::source_fn &s) { return dma_h2d(c, d, n, s); });
     c->server.set_intern([c](const std::string &s) -> uint64_t {
         if (c->intern_used + s.size() + 1 > GF_INTERN_BYTES)
@@ -727,6 +763,7 @@ extern "C" GF_API int gf_wait(gf_handle *h, int *exit_code, int64_t timeout_ns)
         st.rpc_p50_ns = hist_pct(f.lat_hist, 0.50);
         st.rpc_p99_ns = hist_pct(f.lat_hist, 0.99);
         st.regions = f.st_regions;
+        st.region_ns = f.st_region_ns;
         st.heap_alloc = f.heap.n_alloc;
         st.heap_free = f.heap.n_free;
         st.heap_fail = f.heap.n_fail;

@@ -54,6 +54,7 @@ class gf_stats(ctypes.Structure):
         ("rpc_p50_ns", ctypes.c_double),
         ("rpc_p99_ns", ctypes.c_double),
         ("regions", ctypes.c_uint64),
+        ("region_ns", ctypes.c_uint64),
         ("heap_alloc", ctypes.c_uint64),
         ("heap_free", ctypes.c_uint64),
         ("heap_fail", ctypes.c_uint64),

@@ -225,3 +225,39 @@ def test_rpc_timeout_without_server(gf_lib):
             time.sleep(0.01)
         rc, ec = c.wait(h)
     assert ec == 1 and rc == gf.GF_ETIMEDOUT
+
+
+def test_div6_matches_ieee_division(gf_lib, ctx):
+    """gf_div6_rn (Markstein's correction) equals x / 6.0 bit for bit."""
+    import torch
+    rng = np.random.default_rng(6)
+    n = 1 << 22
+    e = rng.integers(-1074, 1024, n).astype(np.float64)
+    m = rng.random(n) + 1.0
+    x = np.ldexp(m, e.astype(np.int64))
+    x[: n // 4] = rng.random(n // 4) * 6.0                       # the Jacobi range
+    x[n // 4: n // 4 + 1000] = np.arange(1000, dtype=np.float64)  # integers and 0
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324, 2.0 ** -1000, 2.0 ** -1000 * (1 - 2 ** -53),
+                        2.0 ** 1001, np.nextafter(2.0 ** 1001, 0), 1.7976931348623157e308, 6.0, 3.0, 12.0])
+    x[-len(special):] = special
+    x[n // 2: n // 2 + 10000] *= -1.0
+    out = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+    rc, ec = ctx.run("div6_probe", [n], [(torch.from_numpy(x).cuda(), 1), (out, 1)])
+    assert ec == 0
+    o = out.cpu().numpy().view(np.uint64).reshape(n, 2)
+    assert np.array_equal(o[:, 0], o[:, 1])
+    ref = (x / 6.0).view(np.uint64)                              # numpy's IEEE division agrees too
+    finite = np.isfinite(x)
+    assert np.array_equal(o[finite, 0], ref[finite])
+
+
+def test_fwrite_append_mode_in_order(gf_lib, tmp_path):
+    import torch
+    gf = gf_lib
+    n = (40 << 20) + 17                                          # several 16 MiB DMA chunks
+    data = np.frombuffer(np.random.default_rng(2).bytes(n), dtype=np.uint8).copy()
+    (tmp_path / "a.bin").write_bytes(b"head")
+    with gf.Context(timeout_ns=10_000_000_000, heap_bytes=64 << 20) as c:
+        rc, ec = c.run("fwrite_modes", [tmp_path / "a.bin", n], [(torch.from_numpy(data).cuda(), 1)])
+    assert ec == 0
+    assert (tmp_path / "a.bin").read_bytes() == b"head" + data.tobytes() * 2
