@@ -179,6 +179,37 @@ GF_API const char *gf_strerror(int err);
  * `block` threads (for sizing, tests and roofline accounting). */
 GF_API int gf_grid_info(gf_ctx *ctx, gf_program prog, uint32_t *sms, uint32_t *blocks_per_sm);
 
+/* ------------------------------------------------------------------ allocation-free reduction */
+
+/* The paper has no counterpart to this entry point; it is an addition for
+ * callers that may not allocate device memory at all (code running under
+ * another framework's fixed memory budget or inside its allocator, code that
+ * must not change the device's footprint, or a one-off reduction that cannot
+ * pay for a gf_ctx, which reserves a heap arena, a pinned ring and state).
+ *
+ * *out (device) = op over x[0 .. n) (device FP64), op one of GF_REDUCE_SUM,
+ * GF_REDUCE_MIN, GF_REDUCE_MAX, computed by the same reduction a gf_reduce
+ * region uses (compensated per-thread sums, warp / block trees, last block
+ * combines the per-block partials in block order), launched on `stream`
+ * (cudaStream_t, NULL = legacy default) and not waited for.  blocks = 0
+ * picks SMs x resident blocks; at most 2048 blocks (larger: GF_EINVAL).
+ * n = 0 stores the identity (0, +inf, -inf).
+ *
+ * Nothing is allocated: the per-block partials live in one static device
+ * array of 32 KiB + 256 B inside this library, present on every GPU that
+ * loads it until the process exits.  All calls share that array and it keeps
+ * the last call's contents; the ticket that must start at zero is cleared
+ * before each launch.  Calls that overlap on the GPU race on the array: do
+ * not run two at once.  The first call on each device looks the array's
+ * address up (cudaGetSymbolAddress, with that device current) and caches it;
+ * make that first call before any stream capture starts.
+ * Errors: GF_EINVAL (bad op, n < 0, NULL pointers, too many blocks),
+ * GF_ECUDA (lookup or launch failed). */
+#define GF_REDUCE_SUM 1
+#define GF_REDUCE_MIN 2
+#define GF_REDUCE_MAX 3
+GF_API int gf_reduce_f64_noalloc(const double *x, int64_t n, int op, double *out, uint32_t blocks, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

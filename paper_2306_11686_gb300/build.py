@@ -23,7 +23,7 @@ NVFLAGS = ARCH + INC + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcom
                         "-Xptxas", "-v", "-diag-suppress", "177"]
 CXXFLAGS = INC + ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-Wall"]
 
-CU = ["runtime.cu", "programs/legacy.cu", "programs/probes.cu", "programs/stress.cu", "programs/batch.cu",
+CU = ["runtime.cu", "noalloc.cu", "programs/legacy.cu", "programs/probes.cu", "programs/stress.cu", "programs/batch.cu",
       "programs/serve.cu"]
 CPP = ["host/server.cpp"]
 HEADERS = ["gf_layout.h", "gf_device.cuh", "gf_device_rpc.cuh", "gf_device_heap.cuh", "gf_program.h",

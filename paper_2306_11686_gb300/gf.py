@@ -104,7 +104,9 @@ _sig = {
     "gf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "gf_grid_info": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32),
                                     ctypes.POINTER(ctypes.c_uint32)]),
+    "gf_reduce_f64_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_uint32, _P]),
 }
+GF_REDUCE_SUM, GF_REDUCE_MIN, GF_REDUCE_MAX = 1, 2, 3
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
     _f.restype = _res
