@@ -139,9 +139,20 @@ def main():
     ap.add_argument("--ref-sweeps", type=int, default=4)
     ap.add_argument("--cpu-sweeps", type=int, default=8)
     ap.add_argument("--out-dir", default=None, help="where the program writes its final grid")
+    ap.add_argument("--sweeps", type=int, default=SWEEPS, help="sweeps per program (100 = the benchmark workload)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-write", action="store_true",
+                    help="the program skips its final fwrite (profiling runs that isolate the sweeps)")
+    ap.add_argument("--workload", default="jacobi", choices=["jacobi", "stress", "batch", "learned", "serve"],
+                    help="jacobi = the benchmark; the others measure the RPC/heap stress, 256-loop batching, "
+                         "learned launch shapes and serving configurations")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "jacobi":
+        from paper_2306_11686_gb300 import measure
+        return measure.run(args)
+    sweeps = args.sweeps
 
     import numpy as np
     import torch
@@ -165,7 +176,7 @@ def main():
     heap = 3 * N ** 3 * 8 + (256 << 20)
     ctx = gf.Context(stream=stream, heap_bytes=heap, heap_small_pct=5,
                      stdout_path=os.path.join(tmp, f"stdout_r{rank}.txt"))
-    argv = [N, SWEEPS, out_path]
+    argv = [N, sweeps, "-" if args.no_write else out_path]
 
     def step(buf):
         rc, ec = ctx.run("jacobi", argv, [(buf, gf.GF_BUF_IN)])
@@ -198,25 +209,27 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total = t.item()
     st = ctx.stats()
-    value = loop_bytes(N, SWEEPS) * args.steps * world / total / 1e9
+    value = loop_bytes(N, sweeps) * args.steps * world / total / 1e9
 
     # ---- e2e: host input staged in by the loader, result written by the program's fwrite
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(1, min(args.steps, 3))
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        step(gh)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_t = e0.elapsed_time(e1) / 1e3
-    e2e = loop_bytes(N, SWEEPS) * e2e_steps * world / e2e_t / 1e9
+    e2e = None
+    if not args.no_e2e:
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2e_steps = max(1, min(args.steps, 3))
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            step(gh)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_t = e0.elapsed_time(e1) / 1e3
+        e2e = loop_bytes(N, sweeps) * e2e_steps * world / e2e_t / 1e9
 
     peak, peak_kind = hbm_peak()
-    achieved = loop_bytes(N, SWEEPS) / (total / args.steps) / 1e9
+    achieved = loop_bytes(N, sweeps) / (total / args.steps) / 1e9
     cpu = None
-    if rank == 0:
+    if rank == 0 and args.cpu_sweeps > 0:
         cv, cdt = cpu_oracle_sample(N, args.cpu_sweeps, tmp)
         cpu = {"value": round(cv, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_sweeps} sweeps of the {N}^3 grid ({cdt:.2f} s)"}
@@ -226,20 +239,22 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"jacobi-7pt {N}^3 fp64, {SWEEPS} sweeps, per-sweep device malloc/free, "
+            "config": {"workload": f"jacobi-7pt {N}^3 fp64, {sweeps} sweeps, per-sweep device malloc/free, "
                                    "fused max-residual, printf per sweep, final fwrite",
                        "grid": st.grid, "block": st.block, "l2": "inputs larger than L2 (2 x 134 MB grids)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": None,
                          "peak_kind": peak_kind, "kernel": "program_kernel<jacobi>"},
-            "e2e": {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": N ** 3 * 8,
+            "e2e": None if e2e is None else {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": N ** 3 * 8,
                     "d2h_bytes_per_step": N ** 3 * 8 + 100 * 24},
             "gpu_launches": args.steps,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
-            "detail": {"main_ns": st.main_ns, "regions": st.regions, "rpc_p50_ns": st.rpc_p50_ns,
-                       "rpc_p99_ns": st.rpc_p99_ns, "rpc_wait_ns": st.rpc_wait_ns,
+            "detail": {"main_ns": st.main_ns, "regions": st.regions, "region_ns": st.region_ns,
+                       "sweep_us": round(st.region_ns / max(1, st.regions) / 1e3, 2),
+                       "sweep_GBps": round(loop_bytes(N, 1) / (st.region_ns / max(1, st.regions) / 1e9) / 1e9, 1),
+                       "rpc_p50_ns": st.rpc_p50_ns, "rpc_p99_ns": st.rpc_p99_ns, "rpc_wait_ns": st.rpc_wait_ns,
                        "step_s": [round(p, 6) for p in per]},
         }
         print(json.dumps(line))

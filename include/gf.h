@@ -65,6 +65,8 @@ typedef struct gf_config {
     const char *stdout_path;      /* where device printf goes (NULL = this process's stdout)       */
     uint32_t fmt_cache;           /* format-string cache entries per instance, power of two (4096) */
     int32_t device;               /* CUDA device ordinal (-1 = current device)                    */
+    uint64_t bulk_bytes;          /* pinned, device-mapped staging arena per instance for large
+                                     fwrite/fread from the serial part (default 64 MiB; 0 = DMA) */
 } gf_config;
 
 /* A buffer mapped into the program before main (the loader's job, paper
@@ -174,6 +176,77 @@ GF_API int gf_get_stats(gf_ctx *ctx, gf_stats *out);
 
 /* Static message for an error code. */
 GF_API const char *gf_strerror(int err);
+
+/* ------------------------------------------------------------------ batching */
+
+/* Graph form of a batch of independent loops (the paper's kernel split, Sec.
+ * 3.3 and Fig. 3, where each parallel region becomes a multi-team kernel the
+ * host launches): n axpy loops z[off_k + i] = a_k * x[off_k + i] +
+ * y[off_k + i], i < trips[k], become one CUDA graph with one kernel node per
+ * loop (no edges, so loops may overlap), each with grid[k] x block[k] threads
+ * (either array may be NULL: 256 threads, enough blocks to cover the loop up
+ * to 8 per SM).  x, y, z are device arrays; trips, a, off, grid, block are
+ * host arrays of n entries.  The graph is built, replayed once to warm up,
+ * then `reps` times on `stream`; *ms receives the mean milliseconds per
+ * replay.  Errors: GF_EINVAL, GF_ECUDA. */
+GF_API int gf_axpy_batch_graph(int n, const int64_t *trips, const double *a, const int64_t *off, const double *x,
+                               const double *y, double *z, const uint32_t *grid, const uint32_t *block, int reps,
+                               void *stream, float *ms);
+
+/* ------------------------------------------------------------------ launch-shape tuning */
+
+/* A synthetic legacy loop (the learned-model workload): per iteration it reads
+ * `bytes` (8..4096, multiple of 8) as bytes/8 coalesced FP64 streams of x,
+ * runs a dependent chain of `flops` FP32 FMAs, a second chain when the
+ * iteration's hash falls below div_thresh (divergent branch; fraction =
+ * div_thresh / 2^32), calls clock() on the host by RPC when another hash
+ * falls below rpc_thresh (rate = rpc_thresh / 2^32), and writes z[i]. */
+typedef struct gf_synth_loop {
+    int64_t trip;
+    uint32_t bytes, flops;
+    uint32_t div_thresh, rpc_thresh;
+    uint64_t seed;
+} gf_synth_loop;
+
+/* A launch shape: grid x block threads (block a multiple of 32, <= 1024);
+ * warps take work items of `chunk` iterations, sched GF 0 = round robin,
+ * 1 = shared counter. */
+typedef struct gf_shape {
+    uint32_t grid, block, chunk, sched;
+} gf_shape;
+
+/* Run loop L once with shape *sh (x: device, >= trip * bytes/8 doubles of
+ * xlen; z: device, >= trip doubles).  Borrows a program instance of ctx for
+ * the loop's RPCs; waits for completion.  Errors: GF_EINVAL (bad loop or
+ * shape, x too short, RPCs without server threads), GF_EBUSY, GF_ECUDA, or a
+ * device error (GF_ETIMEDOUT, GF_ERING). */
+GF_API int gf_synth_run(gf_ctx *ctx, const gf_synth_loop *L, const double *x, uint64_t xlen, double *z,
+                        const gf_shape *sh, void *stream);
+
+/* Time loop L under nshapes shapes: per shape one warm-up run and `reps`
+ * timed runs (CUDA events on `stream`); ms[s] = the fastest, in ms. */
+GF_API int gf_synth_time(gf_ctx *ctx, const gf_synth_loop *L, const double *x, uint64_t xlen, double *z,
+                         const gf_shape *shapes, int nshapes, int reps, void *stream, float *ms);
+
+/* The model's input features of (loop, shape), written to out[GF_TUNE_NFEAT]:
+ * log2 trip, log2 bytes, log2 flops, divergent fraction, 1000 x RPC rate,
+ * log2(grid / sms), log2 block, log2 chunk, sched.  Host only; training and
+ * inference both use this function, so they cannot disagree. */
+#define GF_TUNE_NFEAT 9
+GF_API void gf_tune_features(const gf_synth_loop *L, const gf_shape *sh, uint32_t sms, float *out);
+
+/* FP32 MLP forward pass on the host: normalise each of the nin inputs with
+ * (x - mean) / std, `depth` hidden layers of `width` ReLU units, one linear
+ * output.  params = mean[nin], std[nin], then per hidden layer W (width x in,
+ * row major) and b[width], then w_out[width], b_out.  x is n x nin, y gets n
+ * outputs.  Returns GF_EINVAL for bad sizes. */
+GF_API int gf_mlp_forward(const float *params, int nin, int width, int depth, const float *x, int n, float *y);
+
+/* Learned launch shape: the index of the shape with the smallest predicted
+ * log-time for loop L among shapes[0..nshapes) (the model predicts log
+ * milliseconds from gf_tune_features).  Writes it to *best. */
+GF_API int gf_mlp_choose(const float *params, int width, int depth, const gf_synth_loop *L, const gf_shape *shapes,
+                         int nshapes, uint32_t sms, int *best);
 
 /* Number of SMs and resident blocks per SM that a program's grid uses at
  * `block` threads (for sizing, tests and roofline accounting). */

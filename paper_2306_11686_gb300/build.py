@@ -24,10 +24,10 @@ NVFLAGS = ARCH + INC + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcom
 CXXFLAGS = INC + ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-Wall"]
 
 CU = ["runtime.cu", "noalloc.cu", "programs/legacy.cu", "programs/probes.cu", "programs/stress.cu", "programs/batch.cu",
-      "programs/serve.cu"]
-CPP = ["host/server.cpp"]
+      "programs/synth.cu", "programs/serve.cu"]
+CPP = ["host/server.cpp", "host/mlp.cpp"]
 HEADERS = ["gf_layout.h", "gf_device.cuh", "gf_device_rpc.cuh", "gf_device_heap.cuh", "gf_program.h",
-           "host/server.h", "gf_errors.h"]
+           "host/server.h", "gf_errors.h", "gf_internal.h", "gf_fastdiv.cuh"]
 
 
 def _newer(obj, deps):

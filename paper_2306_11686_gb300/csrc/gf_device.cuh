@@ -38,6 +38,12 @@
 #ifndef GF_BLOCK
 #define GF_BLOCK 256
 #endif
+/* minimum resident blocks per SM the persistent kernel is compiled for
+ * (register cap).  Measured on the Jacobi sweep: 4 (64 registers) ran 6%
+ * slower than leaving the choice to the compiler (80 registers, 3 blocks). */
+#ifndef GF_MIN_BLOCKS
+#define GF_MIN_BLOCKS 1
+#endif
 #define GF_MAX_WARPS (GF_BLOCK / 32)
 
 typedef uint64_t GF_FILE;   /* opaque host FILE* (paper Sec. 3.2: never dereferenced on the device) */
@@ -508,6 +514,96 @@ __device__ int gf_reduce(int64_t b, int64_t e, int sched, int64_t chunk, F body,
     return rc;
 }
 
+/* ====================================================================== batched loops */
+namespace gfd {
+template <class F> struct batch_body {
+    int nloops;
+    const int64_t *trips;
+    const int64_t *prefix;   /* first work item of each loop; prefix[nloops] = items */
+    int64_t chunk;
+    F f;
+};
+
+/* Each warp takes one work item (chunk of one loop) at a time -- from a
+ * shared counter (dynamic) or round robin (static) -- finds its loop by
+ * binary search over the item prefix, and strides its lanes over the chunk. */
+template <class F> __device__ void tramp_batch(const gf_region *rd, const wctx &w)
+{
+    const batch_body<F> bb = *reinterpret_cast<const batch_body<F> *>(rd->body);
+    const uint32_t lane = lane_id();
+    const int64_t items = bb.prefix[bb.nloops];
+    const int64_t warp = w.tid >> 5, nwarps = w.nthreads >> 5;
+    int64_t it = warp;
+    for (;;) {
+        if (rd->sched == GF_SCHED_DYNAMIC) {
+            unsigned long long v = 0;
+            if (lane == 0)
+                v = atomicAdd(&s_st->dyn_next, 1ull);
+            it = (int64_t)__shfl_sync(0xffffffffu, v, 0);
+        }
+        if (it >= items)
+            break;
+        int lo = 0, hi = bb.nloops - 1;               /* last loop whose first item <= it */
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bb.prefix[mid] <= it)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int64_t i0 = (it - bb.prefix[lo]) * bb.chunk;
+        const int64_t i1 = i0 + bb.chunk < bb.trips[lo] ? i0 + bb.chunk : bb.trips[lo];
+        for (int64_t i = i0 + lane; i < i1; i += 32)
+            bb.f(lo, i);
+        if (rd->sched != GF_SCHED_DYNAMIC)
+            it += nwarps;
+    }
+}
+} // namespace gfd
+
+/*
+ * Batching: nloops independent loops in ONE region.  Loop k runs
+ * body(k, i) for i in [0, trips[k]).  Work items are chunks of `chunk`
+ * iterations; a warp runs one item at a time (lanes stride over it), taken
+ * from a shared counter (GF_SCHED_DYNAMIC) or round robin (GF_SCHED_STATIC).
+ * Short and long loops share the grid instead of each being a region with
+ * its own end-of-region wait.  `prefix` is caller-provided device memory of
+ * nloops + 1 entries that receives the item prefix.  Initial thread only
+ * (elsewhere the loops run serially in the caller).
+ */
+template <class F>
+__device__ int gf_parallel_for_batch(int nloops, const int64_t *trips, int64_t *prefix, int64_t chunk, int sched,
+                                     F body)
+{
+    if (chunk < 1)
+        chunk = 1;
+    if (!gfd::is_initial_thread()) {
+        for (int k = 0; k < nloops; k++)
+            for (int64_t i = 0; i < trips[k]; i++)
+                body(k, i);
+        return GF_OK;
+    }
+    int64_t acc = 0;
+    for (int k = 0; k < nloops; k++) {
+        prefix[k] = acc;
+        acc += (trips[k] + chunk - 1) / chunk;
+    }
+    prefix[nloops] = acc;
+    if (acc == 0)
+        return GF_OK;
+    gf_state *S = gfd::s_st;
+    gf_region *r = &S->region;
+    gfd::batch_body<F> bb{nloops, trips, prefix, chunk, body};
+    r->fn = (uint64_t)(&gfd::tramp_batch<F>);
+    r->b = 0;
+    r->e = acc;
+    r->chunk = chunk;
+    r->sched = sched;
+    r->red = GF_RED_NONE;
+    gfd::put_body(r, bb);
+    return gfd::run_region(S);
+}
+
 /* Barrier across every worker of the grid (paper Sec. 3.3: `omp barrier`
  * replaced by a cross-team barrier on global atomic counters).  Inside a
  * region all workers must call it; outside a region it is a no-op. */
@@ -585,7 +681,7 @@ namespace gfd {
 typedef int (*main_t)(int, char **);
 
 template <main_t MAIN>
-__global__ void __launch_bounds__(GF_BLOCK) program_kernel(gf_state *S, int argc, char **argv)
+__global__ void __launch_bounds__(GF_BLOCK, GF_MIN_BLOCKS) program_kernel(gf_state *S, int argc, char **argv)
 {
     if (threadIdx.x == 0)
         s_st = S;

@@ -360,6 +360,168 @@ template <class... A> __device__ inline int64_t rpc(uint32_t op, const char *fmt
     return rpc_issue(op, fmt, a, status);
 }
 
+/* Single-lane asynchronous call for the initial thread: post a slot now,
+ * collect its return later, so the grid can work while the host does. */
+static __device__ __noinline__ int rpc_post1(uint32_t op, const argpack &a, unsigned long long *tk)
+{
+    gf_state *S = s_st;
+    if (a.bytes() > S->slot_bytes - GF_SLOT_PAYLOAD_OFF)
+        return GF_EINVAL;
+    const unsigned long long t = atomicAdd(&S->rpc_ticket, 1ull);
+    uint8_t *slot = (uint8_t *)(S->ring_slots + (t % S->nslots) * (uint64_t)S->slot_bytes);
+    gf_slot_hdr *h = (gf_slot_hdr *)slot;
+    backoff bo(S->timeout_ns);
+    while (ld_acq_sys64(&h->seq) != t)
+        if (!bo.wait()) {
+            set_error(GF_ERING);
+            return GF_ERING;
+        }
+    write_rec(slot + GF_SLOT_PAYLOAD_OFF, a, lane_id(), 0xffffffffu);
+    h->opcode = op;
+    h->nlanes = 1;
+    h->flags = 0;
+    h->fmt_len = 0;
+    h->fmt_key = 0;
+    h->payload_bytes = 0;
+    h->prog = S->prog_id;
+    h->t_issue = now_ns();
+    __threadfence_system();
+    h->t_publish = now_ns();
+    st_rel_sys64(&h->seq, t + 1);
+    *tk = t;
+    return GF_OK;
+}
+
+static __device__ __noinline__ int64_t rpc_finish1(unsigned long long t, int *status)
+{
+    gf_state *S = s_st;
+    uint8_t *slot = (uint8_t *)(S->ring_slots + (t % S->nslots) * (uint64_t)S->slot_bytes);
+    gf_slot_hdr *h = (gf_slot_hdr *)slot;
+    const uint64_t t0 = now_ns();
+    backoff bo(S->timeout_ns);
+    while (ld_acq_sys64(&h->seq) != t + 2)
+        if (!bo.wait()) {
+            set_error(GF_ETIMEDOUT);
+            *status = GF_ETIMEDOUT;
+            return -1;
+        }
+    const int64_t r = (int64_t)ld_vol64((const uint64_t *)(slot + GF_SLOT_RET_OFF));
+    const uint32_t op = h->opcode;
+    atomicAdd((unsigned long long *)&S->st_wait_ns, (unsigned long long)(now_ns() - t0));
+    atomicAdd((unsigned long long *)&S->st_calls[op < GF_NSTAT ? op : 0], 1ull);
+    atomicAdd((unsigned long long *)&S->st_slots[op < GF_NSTAT ? op : 0], 1ull);
+    st_rel_sys64(&h->seq, t + S->nslots);
+    *status = GF_OK;
+    return r;
+}
+
+/* dst[0 .. bytes) = src[...] by the whole grid: 16-byte vector copies when
+ * both ends are 16-byte aligned, bytewise otherwise.  Initial thread only. */
+static __device__ __noinline__ int copy_region(void *dst, const void *src, uint64_t bytes)
+{
+    if ((((uintptr_t)dst | (uintptr_t)src) & 15u) == 0) {
+        const uint64_t n16 = bytes >> 4;
+        uint4 *d = (uint4 *)dst;
+        const uint4 *s = (const uint4 *)src;
+        const int rc = gf_parallel_for(0, (int64_t)n16, GF_SCHED_STATIC, 1, [=](int64_t i) { d[i] = s[i]; });
+        for (uint64_t k = n16 << 4; k < bytes; k++)
+            ((uint8_t *)dst)[k] = ((const uint8_t *)src)[k];
+        return rc;
+    }
+    uint8_t *d = (uint8_t *)dst;
+    const uint8_t *s = (const uint8_t *)src;
+    return gf_parallel_for(0, (int64_t)bytes, GF_SCHED_STATIC, 1, [=](int64_t i) { d[i] = s[i]; });
+}
+
+/*
+ * Large fwrite from the initial thread through the context's bulk arena
+ * (pinned, device-mapped host memory, two halves): the grid copies chunk c
+ * into one half while the host writes chunk c-1 from the other; chunk c is
+ * posted only after chunk c-1 has been written, so the file sees the chunks
+ * in order.  No host-side CUDA call is involved.
+ */
+static __device__ __noinline__ size_t fwrite_bulk(const void *buf, size_t size, size_t n, GF_FILE f)
+{
+    gf_state *S = s_st;
+    const uint64_t bytes = (uint64_t)size * n, half = (S->bulk_bytes / 2) & ~(uint64_t)4095;
+    uint8_t *arena = (uint8_t *)S->bulk_dev;
+    uint64_t written = 0, prev_len = 0;
+    unsigned long long tk = 0;
+    bool pend = false, ok = true;
+    int k = 0;
+    for (uint64_t off = 0; off < bytes && ok; off += half, k ^= 1) {
+        const uint64_t len = bytes - off < half ? bytes - off : half;
+        if (copy_region(arena + (uint64_t)k * half, (const uint8_t *)buf + off, len) != GF_OK)
+            ok = false;
+        if (pend) {
+            int st = GF_OK;
+            const int64_t r = rpc_finish1(tk, &st);
+            pend = false;
+            if (st != GF_OK || r != (int64_t)prev_len)
+                ok = false;
+            else
+                written += prev_len;
+        }
+        if (!ok)
+            break;
+        argpack a;
+        pack_all(a, 1ull, (unsigned long long)len, (unsigned long long)f);
+        a.val(GF_T_ARENA, (uint64_t)k * half);
+        a.val(GF_T_U64, len);
+        if (rpc_post1(GF_OP_FWRITE, a, &tk) != GF_OK)
+            ok = false;
+        else {
+            pend = true;
+            prev_len = len;
+        }
+    }
+    if (pend) {
+        int st = GF_OK;
+        const int64_t r = rpc_finish1(tk, &st);
+        if (st == GF_OK && r == (int64_t)prev_len)
+            written += prev_len;
+    }
+    return (size_t)(written / size);
+}
+
+/* Large fread into device memory through the bulk arena: the host reads
+ * chunk c+1 into one half while the grid copies chunk c out of the other. */
+static __device__ __noinline__ size_t fread_bulk(void *buf, size_t size, size_t n, GF_FILE f)
+{
+    gf_state *S = s_st;
+    const uint64_t bytes = (uint64_t)size * n, half = (S->bulk_bytes / 2) & ~(uint64_t)4095;
+    uint8_t *arena = (uint8_t *)S->bulk_dev;
+    auto post = [&](uint64_t off, int k, unsigned long long *tk) {
+        const uint64_t len = bytes - off < half ? bytes - off : half;
+        argpack a;
+        pack_all(a, 1ull, (unsigned long long)len, (unsigned long long)f);
+        a.val(GF_T_ARENA, (uint64_t)k * half);
+        a.val(GF_T_U64, len);
+        return rpc_post1(GF_OP_FREAD, a, tk);
+    };
+    uint64_t got = 0;
+    unsigned long long tk = 0;
+    if (!bytes || post(0, 0, &tk) != GF_OK)
+        return 0;
+    int k = 0;
+    for (uint64_t off = 0; off < bytes; off += half, k ^= 1) {
+        const uint64_t len = bytes - off < half ? bytes - off : half;
+        int st = GF_OK;
+        const int64_t r = rpc_finish1(tk, &st);
+        if (st != GF_OK || r < 0)
+            break;
+        const bool more = (uint64_t)r == len && off + len < bytes;
+        if (more && post(off + len, k ^ 1, &tk) != GF_OK)
+            break;
+        if (copy_region((uint8_t *)buf + off, arena + (uint64_t)k * half, (uint64_t)r) != GF_OK)
+            break;
+        got += (uint64_t)r;
+        if (!more)
+            break;
+    }
+    return (size_t)(got / size);
+}
+
 } // namespace gfd
 
 /* ====================================================================== libc over RPC */
@@ -388,8 +550,10 @@ __device__ inline int gf_fflush(GF_FILE f)
 {
     return (int)gfd::rpc(GF_OP_FFLUSH, nullptr, nullptr, (unsigned long long)f);
 }
-/* fwrite: small objects travel inside the slot, large ones are read by the
- * host with a copy-engine DMA straight from device memory. */
+/* fwrite: small objects travel inside the slot; large ones from the initial
+ * thread go through the bulk arena (grid copy + host write, overlapped);
+ * large ones from a region's thread are read by the host with a copy-engine
+ * DMA straight from device memory. */
 __device__ inline size_t gf_fwrite(const void *buf, size_t size, size_t n, GF_FILE f)
 {
     const uint64_t bytes = (uint64_t)size * n;
@@ -397,6 +561,8 @@ __device__ inline size_t gf_fwrite(const void *buf, size_t size, size_t n, GF_FI
     if (bytes <= GF_INLINE_BLOB_MAX)
         return (size_t)gfd::rpc(GF_OP_FWRITE, nullptr, nullptr, (unsigned long long)size,
                                 (unsigned long long)n, (unsigned long long)f, gfd::ref_r{buf, (uint32_t)bytes});
+    if (gfd::is_initial_thread() && gfd::s_st->bulk_bytes >= 8192 && size)
+        return gfd::fwrite_bulk(buf, size, n, f);
     return (size_t)gfd::rpc(GF_OP_FWRITE, nullptr, nullptr, (unsigned long long)size, (unsigned long long)n,
                             (unsigned long long)f, gfd::dma_ref{(uint64_t)buf, bytes});
 }
@@ -406,6 +572,8 @@ __device__ inline size_t gf_fread(void *buf, size_t size, size_t n, GF_FILE f)
     if (bytes <= GF_INLINE_BLOB_MAX)
         return (size_t)gfd::rpc(GF_OP_FREAD, nullptr, nullptr, (unsigned long long)size,
                                 (unsigned long long)n, (unsigned long long)f, gfd::ref_w{buf, (uint32_t)bytes});
+    if (gfd::is_initial_thread() && gfd::s_st->bulk_bytes >= 8192 && size)
+        return gfd::fread_bulk(buf, size, n, f);
     size_t r = (size_t)gfd::rpc(GF_OP_FREAD, nullptr, nullptr, (unsigned long long)size, (unsigned long long)n,
                                 (unsigned long long)f, gfd::dma_ref{(uint64_t)buf, bytes});
     __threadfence();

@@ -25,12 +25,16 @@
 #ifndef GF_FASTDIV_CUH
 #define GF_FASTDIV_CUH
 
+/* out of line, so that no part of the general division is hoisted into the
+ * fast path */
+static __device__ __noinline__ double gf_div6_ieee(double x) { return x / 6.0; }
+
 __device__ __forceinline__ double gf_div6_rn(double x)
 {
     const double r = 1.0 / 6.0;                      /* folded at compile time: RN(1/6) */
     const unsigned e = (unsigned)((__double_as_longlong(x) >> 52) & 0x7ff);
     if (e - 23u > 2000u)                             /* outside [2^-1000, 2^1001): IEEE path */
-        return x / 6.0;
+        return gf_div6_ieee(x);
     const double q = __dmul_rn(x, r);
     const double rho = __fma_rn(-q, 6.0, x);
     return __fma_rn(rho, r, q);

@@ -88,6 +88,7 @@ typedef struct gf_rec_hdr {
 #define GF_T_BLOB_W 'w'        /* object written by the host, copied back               */
 #define GF_T_BLOB_RW 'x'       /* object read and written                               */
 #define GF_T_DMA 'D'           /* large object: word = device address, moved by DMA     */
+#define GF_T_ARENA 'A'         /* large object staged in the bulk arena: word = offset  */
 
 #define GF_MAX_ARGS 16
 
@@ -163,6 +164,8 @@ typedef struct gf_state {
     uint64_t fmt_cache;        /* device: open-addressed table of shipped fmt keys    */
     uint32_t fmt_cache_cap, prog_id;
     uint64_t partials;         /* device: nblocks x 16 B reduction partials          */
+    uint64_t bulk_dev;         /* device address of the mapped bulk arena            */
+    uint64_t bulk_bytes;
     uint64_t buf_ptr[GF_MAX_BUFS];
     uint64_t buf_bytes[GF_MAX_BUFS];
     uint32_t nbufs;

@@ -22,10 +22,13 @@ static inline uint64_t now_ns()
 
 void Segment::reset(uint32_t nthreads)
 {
-    head.assign(nthreads, 0);
+    expect.resize(nslots);
+    for (uint32_t s = 0; s < nslots; s++)
+        expect[s] = s;                  /* slot s first carries ticket s */
+    cursor.assign(nthreads, 0);
     for (uint32_t t = 0; t < nthreads; t++)
-        head[t] = t;                    /* thread t serves tickets t, t + nthreads, ... */
-    served.assign(nslots, 0);
+        cursor[t] = t;                  /* thread t serves slots t, t + nthreads, ... */
+    passes.assign(nthreads, 0);
     std::lock_guard<std::mutex> g(fmt_mu);
     fmt_cache.clear();
 }
@@ -263,7 +266,7 @@ int64_t Server::do_printf(const char *fmt, const uint8_t *recp, std::string &out
     return (int64_t)(out.size() - start);
 }
 
-int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec)
+int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *seg)
 {
     RecView r(rec);
     switch (op) {
@@ -317,6 +320,19 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec)
         if (!f || size == 0)
             return 0;
         const uint64_t bytes = size * nmemb;
+        if (r.tag(3) == GF_T_ARENA) {
+            /* staged in the bulk arena by the device grid (fwrite) or to be
+             * copied out of it by the grid (fread) */
+            const uint64_t off = r.word(3);
+            const uint64_t len = r.nargs > 4 ? r.word(4) : 0;
+            if (!seg || !seg->bulk || off + len > seg->bulk_bytes || len < bytes)
+                return 0;
+            std::lock_guard<std::mutex> g(out_mu_);
+            const size_t k = op == GF_OP_FWRITE ? fwrite(seg->bulk + off, size, nmemb, f)
+                                                : fread(seg->bulk + off, size, nmemb, f);
+            stats.dma_bytes += k * size;
+            return (int64_t)k;
+        }
         if (r.tag(3) != GF_T_DMA) {
             uint8_t *b = r.blob(3);
             if (r.blob_len(3) < bytes)
@@ -330,34 +346,10 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec)
         if (op == GF_OP_FWRITE) {
             if (!d2h_)
                 return 0;
-            /* A seekable file not opened for append takes the chunks with
-             * pwrite at their offsets from several threads (page-cache copies
-             * scale with threads); the stdio position is moved past the data
-             * afterwards.  Anything else gets the chunks in order via fwrite. */
-            fflush(f);
-            const int fd = fileno(f);
-            const off_t base = ftello(f);
-            const int fl = fd >= 0 ? fcntl(fd, F_GETFL) : -1;
-            const bool par = base >= 0 && fl >= 0 && !(fl & O_APPEND) && lseek(fd, 0, SEEK_CUR) == base;
-            if (par) {
-                done = d2h_(dev, bytes,
-                            [&](const void *c, uint64_t n, uint64_t pos) {
-                                const uint8_t *p = (const uint8_t *)c;
-                                uint64_t w = 0;
-                                while (w < n) {
-                                    const ssize_t k = pwrite(fd, p + w, n - w, base + (off_t)(pos + w));
-                                    if (k <= 0)
-                                        return false;
-                                    w += (uint64_t)k;
-                                }
-                                return true;
-                            },
-                            true);
-                fseeko(f, base + (off_t)done, SEEK_SET);
-            } else {
-                done = d2h_(dev, bytes, [&](const void *c, uint64_t n, uint64_t) { return fwrite(c, 1, n, f) == n; },
-                            false);
-            }
+            /* chunks arrive in order; each goes to the stream as it lands
+             * while the next one is copied */
+            done = d2h_(dev, bytes, [&](const void *c, uint64_t n, uint64_t) { return fwrite(c, 1, n, f) == n; },
+                        false);
         } else {
             if (!h2d_)
                 return 0;
@@ -402,17 +394,19 @@ int Server::poll(Segment &seg, uint32_t tid, uint32_t nthr)
         return 0;
     const uint32_t N = seg.nslots;
     int served = 0;
-    uint64_t t = seg.head[tid];
     uint32_t gap = 0;
-    /* scan from the lowest unserved ticket; stop after a run of unpublished slots */
-    for (uint64_t scanned = 0; scanned < N && gap < 64; scanned += nthr, t += nthr) {
-        const uint32_t s = (uint32_t)(t % N);
+    /* Claims arrive in ticket order, so the next request is usually in the
+     * slot after the last one served: start there and stop after a run of
+     * quiet slots; every 64th pass scans all of this thread's slots to pick
+     * up requests published late behind the cursor. */
+    const bool full = (++seg.passes[tid] & 63u) == 0;
+    uint32_t s = seg.cursor[tid];
+    for (uint32_t k = 0; k < N; k += nthr, s = (s + nthr) % N) {
+        if (!full && gap >= 64)
+            break;
         uint8_t *slot = seg.slots + (uint64_t)s * seg.slot_bytes;
         gf_slot_hdr *h = (gf_slot_hdr *)slot;
-        if (seg.served[s] == t + 1) {          /* already served, device not yet done with it */
-            gap = 0;
-            continue;
-        }
+        const uint64_t t = seg.expect[s];
         const uint64_t q = acquire_load(&h->seq);
         if (q != t + 1) {
             gap++;
@@ -475,7 +469,7 @@ int Server::poll(Segment &seg, uint32_t tid, uint32_t nthr)
                     ret[l] = -1;
                     continue;
                 }
-                ret[l] = call(op, fmt, pay);
+                ret[l] = call(op, fmt, pay, &seg);
                 pay += rh->bytes;
             }
         }
@@ -485,19 +479,11 @@ int Server::poll(Segment &seg, uint32_t tid, uint32_t nthr)
         stats.records += nl;
         stats.ns += dt;
         stats.per_op[op < GF_NSTAT ? op : 0] += nl;
-        seg.served[s] = t + 1;
+        seg.expect[s] = t + N;
+        seg.cursor[tid] = (s + nthr) % N;
         release_store(&h->seq, t + 2);
         served++;
     }
-    /* advance this thread's head over tickets whose slots the device has released */
-    uint64_t hd = seg.head[tid];
-    for (uint32_t k = 0; k < N; k += nthr) {
-        const uint32_t s = (uint32_t)(hd % N);
-        if (seg.served[s] != hd + 1)
-            break;
-        hd += nthr;
-    }
-    seg.head[tid] = hd;
     return served;
 }
 

@@ -37,10 +37,14 @@ struct Segment {
     uint8_t *slots = nullptr;       /* host address of slot 0                        */
     uint32_t nslots = 0, slot_bytes = 0;
     uint32_t prog = 0;
+    uint8_t *bulk = nullptr;        /* host address of the bulk arena (large fwrite/fread) */
+    uint64_t bulk_bytes = 0;
     std::atomic<bool> active{false};
-    /* per server-thread scan state */
-    std::vector<uint64_t> head;     /* lowest unserved ticket per server thread       */
-    std::vector<uint64_t> served;   /* ticket last served in each slot (+1; 0 = none) */
+    /* scan state: each slot is served for its own next ticket, so a claimant
+     * that never publishes blocks only its slot, not the ring */
+    std::vector<uint64_t> expect;   /* next ticket each slot will carry               */
+    std::vector<uint32_t> cursor;   /* per server thread: slot to start the next scan */
+    std::vector<uint32_t> passes;   /* per server thread: scans so far                */
     std::unordered_map<uint64_t, std::string> fmt_cache;   /* fmt_key -> format */
     std::mutex fmt_mu;
     void reset(uint32_t nthreads);
@@ -89,7 +93,7 @@ class Server {
     HostStats stats;
 
     /* one landing pad: exposed for tests that decode a record by hand */
-    int64_t call(uint32_t opcode, const char *fmt, const uint8_t *rec);
+    int64_t call(uint32_t opcode, const char *fmt, const uint8_t *rec, Segment *seg = nullptr);
 
   private:
     int64_t do_printf(const char *fmt, const uint8_t *rec, std::string &out, uint64_t *stream);

@@ -103,6 +103,11 @@ GF_MAIN(jacobi)(int argc, char **argv)
         owned = un;
         u = un;
     }
+    if (argv[3][0] == '-' && argv[3][1] == 0) {      /* "-": keep the grid, write nothing (profiling) */
+        if (owned)
+            gf_free(owned);
+        return 0;
+    }
     GF_FILE f = gf_fopen(argv[3], "wb");
     if (!f)
         return 3;

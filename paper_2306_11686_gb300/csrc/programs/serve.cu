@@ -1,0 +1,113 @@
+/*
+ * The served legacy program: R passes of a CSR SpMV y = A x (then x = y)
+ * whose row iterations issue libc requests at seeded positions -- fwrite of
+ * self-describing records (16-byte header + payload from the device heap),
+ * printf, clock, getenv.  Many instances run at once under the serving loop
+ * (continuous batching: each takes a free program instance -- its ring
+ * segment and heap arena -- and others are admitted as instances free up).
+ *
+ *   spmv_serve prog R n out_path
+ *   buffers: 0 = int64 rowptr[n+1], 1 = int32 col[nnz], 2 = double val[nnz],
+ *            3 = double x[n] (in: x0, out: the last y), 4 = double y[n] (scratch),
+ *            5 = int64 req[2 nreq] {pass << 32 | row, kind | size << 8} sorted,
+ *            6 = int64 results[nreq]
+ */
+#include "../gf_device.cuh"
+
+static __device__ __forceinline__ uint64_t serve_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;   /* SplitMix64 finaliser */
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+GF_MAIN(spmv_serve)(int argc, char **argv)
+{
+    if (argc < 5)
+        return 2;
+    const unsigned prog = (unsigned)gf_atoll(argv[1]);
+    const int R = (int)gf_atoll(argv[2]);
+    const long long n = gf_atoll(argv[3]);
+    const long long *rowptr = (const long long *)gf_buffer(0);
+    const int *col = (const int *)gf_buffer(1);
+    const double *val = (const double *)gf_buffer(2);
+    double *xb = (double *)gf_buffer(3);
+    double *yb = (double *)gf_buffer(4);
+    const long long *req = (const long long *)gf_buffer(5);
+    long long *res = (long long *)gf_buffer(6);
+    const long long nreq = (long long)(gf_buffer_bytes(5) / 16);
+    if (!rowptr || !col || !val || !xb || !yb || (nreq && (!req || !res)))
+        return 2;
+    GF_FILE f = gf_fopen(argv[4], "wb");
+    if (!f)
+        return 3;
+    double *x = xb, *y = yb;
+    long long q0 = 0;
+    for (int r = 0; r < R; r++) {
+        long long q1 = q0;
+        while (q1 < nreq && (req[2 * q1] >> 32) == r)
+            q1++;
+        const long long qa = q0, qb = q1;
+        const int rr = r;
+        const double *xs = x;
+        double *ys = y;
+        const int rc = gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) {
+            double s = 0.0;
+            for (long long j = rowptr[i]; j < rowptr[i + 1]; j++)
+                s = s + val[j] * xs[col[j]];
+            ys[i] = s;
+            if (qa == qb)
+                return;
+            const long long key = ((long long)rr << 32) | (long long)i;
+            long long lo = qa, hi = qb;                 /* first request with key >= (pass, row) */
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if (req[2 * mid] < key)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            for (long long q = lo; q < qb && req[2 * q] == key; q++) {
+                const int kind = (int)(req[2 * q + 1] & 0xff);
+                const unsigned size = (unsigned)(req[2 * q + 1] >> 8);
+                if (kind == 0) {
+                    const unsigned long long words = (size + 7) / 8;
+                    unsigned long long *b = (unsigned long long *)gf_malloc(16 + 8 * words);
+                    if (!b) {
+                        res[q] = -2;
+                        continue;
+                    }
+                    b[0] = (unsigned long long)prog | ((unsigned long long)rr << 32);
+                    b[1] = (unsigned long long)i | ((unsigned long long)size << 32);
+                    const uint64_t k0 = serve_mix(((uint64_t)prog << 40) ^ ((uint64_t)rr << 32) ^ (uint64_t)i);
+                    for (unsigned long long w = 0; w < words; w++)
+                        b[2 + w] = serve_mix(k0 + w * 0x9E3779B97F4A7C15ull);
+                    res[q] = (long long)gf_fwrite(b, 1, 16 + (size_t)size, f);
+                    gf_free(b);
+                } else if (kind == 1) {
+                    res[q] = gf_printf("p %d r %d row %d y %.17g\n", (int)prog, rr, (int)i, s);
+                } else if (kind == 2) {
+                    res[q] = gf_clock();
+                } else {
+                    char name[16] = "GF_SERVE_VAR0";
+                    name[12] = (char)('0' + (int)(i % 3));
+                    const char *v = gf_getenv(name);
+                    res[q] = v ? (long long)gf_strlen(v) : -1;
+                }
+            }
+        });
+        if (rc)
+            return 10;
+        q0 = q1;
+        double *t = x;
+        x = y;
+        y = t;
+    }
+    if (x != xb) {                                       /* the last y lives in the scratch buffer */
+        const double *src = x;
+        if (gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) { xb[i] = src[i]; }))
+            return 10;
+    }
+    gf_fclose(f);
+    return 0;
+}

@@ -31,6 +31,7 @@
 
 #include "gf.h"
 #include "gf_layout.h"
+#include "gf_internal.h"
 #include "gf_program.h"
 #include "host/server.h"
 
@@ -86,6 +87,8 @@ struct Instance {
     uint32_t nslabs = 0, npages = 0;
     uint64_t slab_bytes = 0, large_bytes = 0;
     char *d_argv = nullptr;
+    uint8_t *bulk_host = nullptr;   /* pinned, device-mapped bulk arena */
+    uint64_t bulk_dev = 0;
     std::vector<char> h_argv;
     gf_state h_init;     /* initial state copied to the device at launch */
     gf_state h_final;    /* state read back after the program ends       */
@@ -161,6 +164,7 @@ extern "C" GF_API void gf_config_default(gf_config *c)
     c->stream = nullptr;
     c->stdout_path = nullptr;
     c->fmt_cache = 4096;
+    c->bulk_bytes = 64ull << 20;
     c->device = -1;
 }
 
@@ -331,6 +335,16 @@ static int inst_alloc(gf_ctx *c, Instance *in)
     in->seg.slot_bytes = cf.slot_bytes;
     in->seg.prog = (uint32_t)in->idx;
     in->seg.slots = c->ring_host + (size_t)in->idx * cf.ring_slots * cf.slot_bytes;
+    if (cf.bulk_bytes) {
+        if (cudaHostAlloc((void **)&in->bulk_host, cf.bulk_bytes, cudaHostAllocMapped | cudaHostAllocPortable) !=
+            cudaSuccess)
+            return GF_ENOMEM;
+        void *bd = nullptr;
+        GF_CK(cudaHostGetDevicePointer(&bd, in->bulk_host, 0));
+        in->bulk_dev = (uint64_t)bd;
+        in->seg.bulk = in->bulk_host;
+        in->seg.bulk_bytes = cf.bulk_bytes;
+    }
     return GF_OK;
 }
 
@@ -340,6 +354,8 @@ static void inst_free(Instance *in)
     cudaFree(in->d_partials);
     cudaFree(in->d_fmt);
     cudaFree(in->d_argv);
+    if (in->bulk_host)
+        cudaFreeHost(in->bulk_host);
     cudaFree(in->d_heap);
     cudaFree(in->d_meta);
     cudaFree(in->d_heads);
@@ -534,6 +550,8 @@ static void release_staged(gf_handle *h, bool copy_back)
     h->staged.clear();
 }
 
+static int inst_start(gf_ctx *c, Instance *in, cudaStream_t stream, uint32_t grid);
+
 extern "C" GF_API int gf_launch(gf_ctx *c, gf_program prog, int argc, const char *const *argv, const gf_buf *bufs,
                                 int nbufs, void *stream, uint32_t grid, gf_handle **out)
 {
@@ -622,6 +640,28 @@ extern "C" GF_API int gf_launch(gf_ctx *c, gf_program prog, int argc, const char
         s.buf_bytes[k] = bufs[k].bytes;
     }
     s.nbufs = (uint32_t)nbufs;
+    if ((rc = inst_start(c, in, h->stream, grid)) != GF_OK)
+        return bail(rc);
+    int a_argc = argc;
+    char **a_argv = (char **)in->d_argv;
+    gf_state *a_state = in->d_state;
+    void *args[3] = {&a_state, &a_argc, &a_argv};
+    cudaError_t le = pe.launch(args, grid, GF_BLOCK_THREADS, h->stream);
+    if (le != cudaSuccess || cudaEventRecord(in->ev_done, h->stream) != cudaSuccess) {
+        fprintf(stderr, "gf: launch of %s failed: %s\n", pe.name.c_str(), cudaGetErrorString(le));
+        in->seg.active = false;
+        c->nactive--;
+        return bail(GF_ECUDA);
+    }
+    *out = h;
+    return GF_OK;
+}
+
+/* Fill the rest of in->h_init (buffers are already in it), copy it to the
+ * device, reset the heap metadata, reset and activate the ring segment. */
+static int inst_start(gf_ctx *c, Instance *in, cudaStream_t stream, uint32_t grid)
+{
+    gf_state &s = in->h_init;
     s.nblocks = grid;
     s.block_dim = GF_BLOCK_THREADS;
     s.nworkers = grid * GF_BLOCK_THREADS - 32;
@@ -634,6 +674,8 @@ extern "C" GF_API int gf_launch(gf_ctx *c, gf_program prog, int argc, const char
     s.fmt_cache_cap = c->cfg.fmt_cache;
     s.prog_id = (uint32_t)in->idx;
     s.partials = (uint64_t)in->d_partials;
+    s.bulk_dev = in->bulk_dev;
+    s.bulk_bytes = in->bulk_host ? c->cfg.bulk_bytes : 0;
     gf_heap &H = s.heap;
     H.base = (uint64_t)in->d_heap;
     H.bytes = in->slab_bytes + in->large_bytes;
@@ -650,14 +692,14 @@ extern "C" GF_API int gf_launch(gf_ctx *c, gf_program prog, int argc, const char
     H.npages = in->npages;
     H.large_next = in->npages ? 1 : 0;
     in->h_ext0 = (uint64_t)0 | ((uint64_t)in->npages << 32);
-    if (cudaMemcpyAsync(in->d_state, &s, sizeof s, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(in->d_meta, 0, (size_t)std::max<uint32_t>(in->nslabs, 1) * 16, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(in->d_heads, 0, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 8, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(in->d_cur, 0, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 4, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(in->d_lsize, 0, (size_t)std::max<uint32_t>(in->npages, 1) * 4, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(in->d_fmt, 0, (size_t)c->cfg.fmt_cache * 8, h->stream) != cudaSuccess ||
-        cudaMemcpyAsync(in->d_ext, &in->h_ext0, 8, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
-        return bail(GF_ECUDA);
+    if (cudaMemcpyAsync(in->d_state, &s, sizeof s, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemsetAsync(in->d_meta, 0, (size_t)std::max<uint32_t>(in->nslabs, 1) * 16, stream) != cudaSuccess ||
+        cudaMemsetAsync(in->d_heads, 0, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 8, stream) != cudaSuccess ||
+        cudaMemsetAsync(in->d_cur, 0, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 4, stream) != cudaSuccess ||
+        cudaMemsetAsync(in->d_lsize, 0, (size_t)std::max<uint32_t>(in->npages, 1) * 4, stream) != cudaSuccess ||
+        cudaMemsetAsync(in->d_fmt, 0, (size_t)c->cfg.fmt_cache * 8, stream) != cudaSuccess ||
+        cudaMemcpyAsync(in->d_ext, &in->h_ext0, 8, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return GF_ECUDA;
     /* ring segment: every slot free for its first ticket */
     const uint32_t nthr = std::max<uint32_t>(1, c->cfg.server_threads);
     for (uint32_t k = 0; k < in->seg.nslots; k++) {
@@ -668,20 +710,43 @@ extern "C" GF_API int gf_launch(gf_ctx *c, gf_program prog, int argc, const char
     in->seg.active.store(true, std::memory_order_release);
     c->nactive++;
     c->act_cv.notify_all();
-    int a_argc = argc;
-    char **a_argv = (char **)in->d_argv;
-    gf_state *a_state = in->d_state;
-    void *args[3] = {&a_state, &a_argc, &a_argv};
-    cudaError_t le = pe.launch(args, grid, GF_BLOCK_THREADS, h->stream);
-    if (le != cudaSuccess || cudaEventRecord(in->ev_done, h->stream) != cudaSuccess) {
-        fprintf(stderr, "gf: launch of %s failed: %s\n", pe.name.c_str(), cudaGetErrorString(le));
-        in->seg.active = false;
-        c->nactive--;
-        return bail(GF_ECUDA);
-    }
-    *out = h;
     return GF_OK;
 }
+
+/* Standalone kernels that use the device runtime's RPC or heap (synthetic
+ * loops, the graph executor) borrow an instance: its state initialised with
+ * no program and no buffers, its ring segment served.  Returns the device
+ * state, or nullptr when every instance is taken. */
+gf_state *gf_inst_acquire(gf_ctx *c, void *stream, uint32_t nblocks, int *idx)
+{
+    for (Instance *x : c->inst) {
+        bool f = false;
+        if (x->busy.compare_exchange_strong(f, true)) {
+            memset(&x->h_init, 0, sizeof x->h_init);
+            cudaStream_t s = (cudaStream_t)(stream ? stream : c->own_stream);
+            if (inst_start(c, x, s, nblocks ? nblocks : 1) != GF_OK || cudaStreamSynchronize(s) != cudaSuccess) {
+                x->seg.active = false;
+                x->busy = false;
+                return nullptr;
+            }
+            *idx = x->idx;
+            return x->d_state;
+        }
+    }
+    return nullptr;
+}
+
+/* The caller has drained its stream: stop serving the segment, free the instance. */
+void gf_inst_release(gf_ctx *c, int idx)
+{
+    Instance *in = c->inst[(size_t)idx];
+    if (in->seg.active.exchange(false))
+        c->nactive--;
+    in->busy = false;
+}
+
+int gf_ctx_server_threads(gf_ctx *c) { return (int)c->cfg.server_threads; }
+void *gf_inst_scratch(gf_ctx *c, int idx) { return c->inst[(size_t)idx]->d_partials; }
 
 extern "C" GF_API int gf_done(gf_handle *h)
 {

@@ -38,6 +38,7 @@ class gf_config(ctypes.Structure):
         ("stdout_path", ctypes.c_char_p),
         ("fmt_cache", ctypes.c_uint32),
         ("device", ctypes.c_int32),
+        ("bulk_bytes", ctypes.c_uint64),
     ]
 
 
@@ -84,6 +85,18 @@ class gf_serve_opts(ctypes.Structure):
     _fields_ = [("timeout_ns", ctypes.c_int64), ("stop", ctypes.POINTER(ctypes.c_int32))]
 
 
+class gf_synth_loop(ctypes.Structure):
+    _fields_ = [("trip", ctypes.c_int64), ("bytes", ctypes.c_uint32), ("flops", ctypes.c_uint32),
+                ("div_thresh", ctypes.c_uint32), ("rpc_thresh", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+class gf_shape(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_uint32), ("block", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
+                ("sched", ctypes.c_uint32)]
+
+
+GF_TUNE_NFEAT = 9
+
 gf_host_fn = ctypes.CFUNCTYPE(ctypes.c_int64, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p)
 
 _P = ctypes.c_void_p
@@ -105,6 +118,17 @@ _sig = {
     "gf_grid_info": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32),
                                     ctypes.POINTER(ctypes.c_uint32)]),
     "gf_reduce_f64_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, _P, ctypes.c_uint32, _P]),
+    "gf_synth_run": (ctypes.c_int, [_P, ctypes.POINTER(gf_synth_loop), _P, ctypes.c_uint64, _P,
+                                    ctypes.POINTER(gf_shape), _P]),
+    "gf_synth_time": (ctypes.c_int, [_P, ctypes.POINTER(gf_synth_loop), _P, ctypes.c_uint64, _P,
+                                     ctypes.POINTER(gf_shape), ctypes.c_int, ctypes.c_int, _P, ctypes.c_void_p]),
+    "gf_tune_features": (None, [ctypes.POINTER(gf_synth_loop), ctypes.POINTER(gf_shape), ctypes.c_uint32, _P]),
+    "gf_mlp_forward": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P]),
+    "gf_mlp_choose": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(gf_synth_loop),
+                                     ctypes.POINTER(gf_shape), ctypes.c_int, ctypes.c_uint32,
+                                     ctypes.POINTER(ctypes.c_int)]),
+    "gf_axpy_batch_graph": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P,
+                                           ctypes.POINTER(ctypes.c_float)]),
 }
 GF_REDUCE_SUM, GF_REDUCE_MIN, GF_REDUCE_MAX = 1, 2, 3
 for _name, (_res, _args) in _sig.items():

@@ -93,6 +93,53 @@ def jacobi_input(n: int, seed: int = 2) -> np.ndarray:
     return np.ascontiguousarray(g.reshape(-1))
 
 
+def loops_inputs(n: int = 256, seed: int = 3, lo: int = 1 << 10, hi: int = 1 << 22):
+    """n independent axpy loops: trip counts log-uniform per octave in [lo, hi],
+    coefficients a_k ~ U[-1,1), slices packed back to back in x, y, z.
+    Returns (trips int64[n], a float64[n], off int64[n], x, y) with x, y ~ U[-1,1)."""
+    trips = loguniform_int(seed, n, lo, hi).astype(np.int64)
+    a = uniform_pm1(seed + 1000, n)
+    off = np.zeros(n, dtype=np.int64)
+    off[1:] = np.cumsum(trips)[:-1]
+    total = int(trips.sum())
+    x = uniform_pm1(seed + 2000, total)
+    y = uniform_pm1(seed + 3000, total)
+    return trips, a, off, x, y
+
+
+def serve_program_inputs(p: int, n: int = 1 << 20, nnz_row: int = 16, passes: int = 10, req_per_pass: int = 64,
+                         seed_base: int = 5):
+    """Program p of the serving workload: CSR matrix with n rows, nnz_row
+    nonzeros per row at uniform random columns, values and x0 ~ U[-1,1)
+    (stream seed_base + p), and libc requests at Poisson row positions
+    (geometric gaps with mean n / req_per_pass) in every pass, kinds uniform
+    over {fwrite, printf, clock, getenv}, fwrite sizes per-octave log-uniform
+    in [64 B, 1 MiB].  Returns (rowptr, col, val, x0, req) with req an int64
+    array of pairs (pass << 32 | row, kind | size << 8) sorted by key."""
+    seed = seed_base + p
+    nnz = n * nnz_row
+    rowptr = np.arange(0, nnz + 1, nnz_row, dtype=np.int64)
+    col = uniform_int(seed, nnz, 0, n - 1).astype(np.int32)
+    val = uniform_pm1(seed + 100, nnz)
+    x0 = uniform_pm1(seed + 200, n)
+    keys, types = [], []
+    for r in range(passes):
+        u = uniform01(seed * 1000 + r, 4 * req_per_pass + 16)
+        q = req_per_pass / n                                     # success probability per row
+        gaps = 1 + np.floor(np.log1p(-u) / np.log1p(-q)).astype(np.int64)
+        rows = np.cumsum(gaps) - 1
+        rows = rows[rows < n]
+        kind = uniform_int(seed * 1000 + r + 500, len(rows), 0, 3)
+        size = loguniform_int(seed * 1000 + r + 700, len(rows), 64, 1 << 20)
+        keys.append((np.int64(r) << 32) | rows)
+        types.append(kind.astype(np.int64) | (size.astype(np.int64) << 8))
+    key = np.concatenate(keys) if keys else np.zeros(0, dtype=np.int64)
+    typ = np.concatenate(types) if types else np.zeros(0, dtype=np.int64)
+    req = np.empty(2 * len(key), dtype=np.int64)
+    req[0::2], req[1::2] = key, typ
+    return rowptr, col, val, x0, req
+
+
 def write_f64(path: str, a: np.ndarray) -> None:
     np.ascontiguousarray(a, dtype=np.float64).tofile(path)
 

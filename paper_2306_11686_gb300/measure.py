@@ -1,0 +1,146 @@
+"""Measurements of the non-benchmark configurations (used by bench.py --workload).
+
+Each function prints one JSON line with its own metric:
+  stress   printf calls/s with warp aggregation on vs off (printf-only loop,
+           2^20 iterations x 4 calls), device RPC p50/p99, heap alloc/free
+           pairs/s (2^20 x 8 pairs, log-uniform 16 B..64 KiB), the full
+           stress program's time;
+  batch    256 axpy loops (trip 2^10..2^22): one region per loop vs one
+           batched region vs one CUDA graph; loop GB/s (24 B per iteration);
+  learned  autotuner + MLP over 2000 synthetic loops (1600 train / 400
+           held out): regret vs the autotuner's optimum, speedup vs the plain
+           runtime's fixed shape;
+  serve    64 served programs (CSR SpMV, 1M rows, 16 nnz/row, 10 passes,
+           ~64 libc requests per pass) under continuous batching: calls/s,
+           RPC p50/p99, admission -> done latency, SpMV GB/s.
+"""
+from __future__ import annotations
+
+import json
+import os
+import shutil
+import tempfile
+import time
+
+import numpy as np
+
+from . import gf, inputs
+
+
+def _timed_run(ctx, stream, name, argv, bufs):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc, ec = ctx.run(name, argv, bufs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ec != 0:
+        raise RuntimeError(f"{name} exit code {ec}")
+    return e0.elapsed_time(e1) / 1e3
+
+
+def stress(args):
+    import torch
+    T = 1 << 20
+    tmp = tempfile.mkdtemp(prefix="gfstress")
+    sizes = torch.from_numpy(inputs.loguniform_int(3, 8 * T, 16, 65536).astype(np.int32)).cuda()
+    cs = torch.zeros(T, dtype=torch.int64, device="cuda")
+    fails = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    out = {}
+    for agg in (1, 0):
+        with gf.Context(aggregate=agg, stream=stream, heap_bytes=8 << 30, heap_small_pct=95, server_threads=4,
+                        stdout_path=os.path.join(tmp, "out.txt"), timeout_ns=int(120e9)) as ctx:
+            _timed_run(ctx, stream, "printf_only", [1 << 14], [])          # warm-up
+            t = _timed_run(ctx, stream, "printf_only", [T], [])
+            st = ctx.stats()
+            out[agg] = dict(calls_per_s=4 * T / t, seconds=t, p50_ns=st.rpc_p50_ns, p99_ns=st.rpc_p99_ns,
+                            slots=int(st.rpc_slots[gf.OP_PRINTF]), calls=int(st.rpc_calls[gf.OP_PRINTF]))
+            if agg:
+                th = _timed_run(ctx, stream, "heap_only", [T], [(sizes, 1), (cs, 1), (fails, 1)])
+                hst = ctx.stats()
+                ts = _timed_run(ctx, stream, "stress", [T], [(sizes, 1), (cs, 1), (fails, 1)])
+                sst = ctx.stats()
+    line = {"metric": "RPC calls/s + p99 latency", "value": round(out[1]["calls_per_s"]), "unit": "calls/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "int/bytes", "data": "synthetic",
+            "config": {"workload": "2^20 iterations x 4 printf (int/double formats), host server 4 threads"},
+            "detail": {"aggregated": out[1], "per_thread": out[0],
+                       "aggregation_speedup": out[1]["calls_per_s"] / out[0]["calls_per_s"],
+                       "heap_pairs_per_s": 8 * T / th, "heap_fail": int(hst.heap_fail),
+                       "stress_program_s": ts, "stress_slots": int(sst.rpc_slots[gf.OP_PRINTF]),
+                       "stress_calls": int(sst.rpc_calls[gf.OP_PRINTF])}}
+    print(json.dumps(line))
+    shutil.rmtree(tmp, ignore_errors=True)
+
+
+def batch(args):
+    import ctypes
+    import torch
+    trips, a, off, x, y = inputs.loops_inputs()
+    n, total = len(trips), int(trips.sum())
+    dv = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()
+    td, ad, od, xd, yd = dv(trips), dv(a), dv(off), dv(x), dv(y)
+    z = torch.zeros(total, dtype=torch.float64, device="cuda")
+    prefix = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    res = {}
+    with gf.Context(stream=stream, heap_bytes=64 << 20, timeout_ns=int(60e9)) as ctx:
+        for label, argv in [("regions", [0, n, 1, 0]), ("batched_dynamic", [1, n, 4096, 1]),
+                            ("batched_static", [1, n, 4096, 0])]:
+            bufs = [(td, 1), (ad, 1), (od, 1), (xd, 1), (yd, 1), (z, 1), (prefix, 1)]
+            _timed_run(ctx, stream, "loops", argv, bufs)
+            ts = [_timed_run(ctx, stream, "loops", argv, bufs) for _ in range(3)]
+            st = ctx.stats()
+            res[label] = {"program_s": min(ts), "region_s": st.region_ns / 1e9, "regions": int(st.regions),
+                          "GBps_regions": 24 * total / (st.region_ns / 1e9) / 1e9}
+    ms = ctypes.c_float()
+    P = lambda arr: ctypes.c_void_p(arr.ctypes.data)
+    rc = gf.gf_axpy_batch_graph(n, P(trips), P(a), P(off), ctypes.c_void_p(xd.data_ptr()),
+                                ctypes.c_void_p(yd.data_ptr()), ctypes.c_void_p(z.data_ptr()), None, None, 5,
+                                ctypes.c_void_p(stream.cuda_stream), ctypes.byref(ms))
+    res["graph"] = {"replay_s": ms.value / 1e3, "GBps": 24 * total / (ms.value / 1e3) / 1e9, "rc": rc}
+    best = res["batched_dynamic"]["GBps_regions"]
+    line = {"metric": "loop GB/s (% HBM peak)", "value": round(best, 1), "unit": "GB/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{n} axpy loops, trip log-uniform 2^10..2^22, {total} iterations, 24 B/iter"},
+            "detail": res}
+    print(json.dumps(line))
+
+
+def learned(args):
+    from . import tune
+    res = tune.run(n_loops=2000, n_train=1600, reps=2, epochs=300, log=lambda m: print("#", m, flush=True),
+                   out=os.path.join(args.out_dir or ".", "learned_ds.npz") if args.out_dir else None)
+    line = {"metric": "learned vs plain config", "value": round(res["mean_regret"], 4), "unit": "mean regret",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "fp32 model", "data": "synthetic",
+            "config": {"workload": "2000 synthetic loops (1600 train / 400 held out), 96 launch shapes"},
+            "detail": res}
+    print(json.dumps(line))
+
+
+def serve_run(args):
+    from . import serve
+    P, n = 64, 1 << 20
+    os.environ.setdefault("GF_SERVE_VAR0", "zero")
+    os.environ.setdefault("GF_SERVE_VAR1", "one-1")
+    os.environ.pop("GF_SERVE_VAR2", None)
+    tmp = tempfile.mkdtemp(prefix="gfserve", dir=args.out_dir)
+    t0 = time.time()
+    progs = [serve.Program(p, n, 10, 64) for p in range(P)]
+    t_gen = time.time() - t0
+    outs = [os.path.join(tmp, f"rec{p}.bin") for p in range(P)]
+    recs, agg = serve.serve(progs, outs, max_concurrent=16, rate_hz=400.0, heap_bytes=1 << 30, ring_slots=1024,
+                            server_threads=4, stdout_path=os.path.join(tmp, "out.txt"))
+    agg["input_gen_s"] = t_gen
+    agg["errors"] = sum(1 for r in recs if r["rc"] or r["exit"])
+    line = {"metric": "RPC calls/s + p99 latency", "value": round(agg["calls_per_s"]), "unit": "calls/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "64 programs, CSR SpMV 1M rows x 16 nnz, 10 passes, Poisson libc requests, "
+                                   "16 concurrent instances, arrivals 400/s"},
+            "detail": agg}
+    print(json.dumps(line))
+    shutil.rmtree(tmp, ignore_errors=True)
+
+
+def run(args):
+    {"stress": stress, "batch": batch, "learned": learned, "serve": serve_run}[args.workload](args)

@@ -1,0 +1,197 @@
+"""Autotuner and learned launch-shape model for synthetic legacy loops.
+
+Pipeline (the learned-model pattern on top of the runtime):
+  1. `measure`: the autotuner times every candidate shape of every loop
+     natively (gf_synth_time: CUDA events, fastest of `reps` runs after a
+     warm-up); its per-loop optimum is the judge of regret.
+  2. `train`: an FP32 MLP (3 hidden layers of 64 ReLU units) learns log(ms)
+     from gf_tune_features(loop, shape) on the training loops (torch).
+  3. `evaluate`: on held-out loops the model's choice (gf_mlp_choose, the C++
+     forward pass) is compared with the autotuner's optimum:
+     regret = t(model's shape) / t(best measured shape) - 1; also against the
+     plain runtime's fixed shape (the heuristic fallback).
+
+Feature extraction and inference are the library's own (C ABI); Python only
+orchestrates and trains.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import gf, inputs
+
+WIDTH, DEPTH = 64, 3
+GRID_MULT = (1, 2, 4, 8)          # blocks per SM
+BLOCKS = (128, 256, 512, 1024)
+CHUNKS = (64, 512, 4096)
+SCHEDS = (0, 1)
+
+
+def shapes(sms: int):
+    out = []
+    for gm in GRID_MULT:
+        for b in BLOCKS:
+            for c in CHUNKS:
+                for s in SCHEDS:
+                    out.append((gm * sms, b, c, s))
+    return out
+
+
+def heuristic_shape(sms: int):
+    """The plain runtime's fixed choice: 4 blocks of 256 per SM, small static items."""
+    return (4 * sms, 256, 64, 0)
+
+
+def config4_loops(n: int = 2000, seed: int = 4):
+    """trip log-uniform 2^10..2^26, bytes/iter in {8..256}, flops 1..64,
+    divergent fraction U[0, 0.5], RPC rate U[0, 1e-3] (as thresholds of 2^32)."""
+    trip = inputs.loguniform_int(seed, n, 1 << 10, 1 << 26).astype(np.int64)
+    bytes_ = np.array([8, 16, 32, 64, 128, 256], dtype=np.int64)[inputs.uniform_int(seed + 1, n, 0, 5)]
+    flops = inputs.uniform_int(seed + 2, n, 1, 64)
+    div = inputs.uniform01(seed + 3, n) * 0.5
+    rpc = inputs.uniform01(seed + 4, n) * 1e-3
+    loops = []
+    for k in range(n):
+        loops.append(dict(trip=int(trip[k]), bytes=int(bytes_[k]), flops=int(flops[k]),
+                          div_thresh=int(div[k] * 2 ** 32), rpc_thresh=int(rpc[k] * 2 ** 32), seed=1000 + k))
+    return loops
+
+
+def c_loop(d):
+    L = gf.gf_synth_loop()
+    L.trip, L.bytes, L.flops = d["trip"], d["bytes"], d["flops"]
+    L.div_thresh, L.rpc_thresh, L.seed = d["div_thresh"], d["rpc_thresh"], d["seed"]
+    return L
+
+
+def c_shapes(shs):
+    arr = (gf.gf_shape * len(shs))()
+    for k, (g, b, c, s) in enumerate(shs):
+        arr[k].grid, arr[k].block, arr[k].chunk, arr[k].sched = g, b, c, s
+    return arr
+
+
+def features(loop, shs, sms):
+    L = c_loop(loop)
+    out = np.zeros((len(shs), gf.GF_TUNE_NFEAT), dtype=np.float32)
+    sa = c_shapes(shs)
+    for k in range(len(shs)):
+        gf.gf_tune_features(ctypes.byref(L), ctypes.byref(sa[k]), sms, out[k].ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def measure(ctx, loops, shs, x, z, reps=2, stream=None, log=None):
+    """ms[loop, shape] from the native timer."""
+    ms = np.zeros((len(loops), len(shs)), dtype=np.float32)
+    sa = c_shapes(shs)
+    xlen = x.numel()
+    t0 = time.time()
+    for k, d in enumerate(loops):
+        L = c_loop(d)
+        row = (ctypes.c_float * len(shs))()
+        rc = gf.gf_synth_time(ctx.h, ctypes.byref(L), ctypes.c_void_p(x.data_ptr()), xlen,
+                              ctypes.c_void_p(z.data_ptr()), sa, len(shs), reps, stream, row)
+        if rc != gf.GF_OK:
+            raise gf.GFError(rc, f"gf_synth_time(loop {k})")
+        ms[k] = np.frombuffer(row, dtype=np.float32)
+        if log and (k + 1) % 100 == 0:
+            log(f"measured {k + 1}/{len(loops)} loops in {time.time() - t0:.1f} s")
+    return ms
+
+
+def train(X, y, epochs=300, seed=0, device=None, log=None):
+    """FP32 MLP (3 x 64 ReLU) regression of log(ms); returns the flat parameter
+    vector in gf_mlp_forward's layout."""
+    import torch
+    torch.manual_seed(seed)
+    dev = device or ("cuda" if torch.cuda.is_available() else "cpu")
+    mean = X.mean(0)
+    sd = X.std(0) + 1e-6
+    Xt = torch.from_numpy((X - mean) / sd).float().to(dev)
+    yt = torch.from_numpy(y).float().to(dev)
+    layers, d = [], X.shape[1]
+    for _ in range(DEPTH):
+        layers += [torch.nn.Linear(d, WIDTH), torch.nn.ReLU()]
+        d = WIDTH
+    layers.append(torch.nn.Linear(d, 1))
+    net = torch.nn.Sequential(*layers).to(dev)
+    opt = torch.optim.Adam(net.parameters(), lr=2e-3)
+    sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, epochs)
+    n = Xt.shape[0]
+    bs = 4096
+    for ep in range(epochs):
+        perm = torch.randperm(n, device=dev)
+        tot = 0.0
+        for i in range(0, n, bs):
+            idx = perm[i:i + bs]
+            loss = torch.mean((net(Xt[idx]).squeeze(1) - yt[idx]) ** 2)
+            opt.zero_grad()
+            loss.backward()
+            opt.step()
+            tot += loss.item() * len(idx)
+        sched.step()
+        if log and (ep + 1) % 50 == 0:
+            log(f"epoch {ep + 1}: mse {tot / n:.4f}")
+    parts = [mean.astype(np.float32), sd.astype(np.float32)]
+    for m in net:
+        if isinstance(m, torch.nn.Linear):
+            parts += [m.weight.detach().cpu().numpy().astype(np.float32).reshape(-1),
+                      m.bias.detach().cpu().numpy().astype(np.float32).reshape(-1)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def choose(params, loop, shs, sms):
+    best = ctypes.c_int(-1)
+    rc = gf.gf_mlp_choose(params.ctypes.data_as(ctypes.c_void_p), WIDTH, DEPTH, ctypes.byref(c_loop(loop)),
+                          c_shapes(shs), len(shs), sms, ctypes.byref(best))
+    if rc != gf.GF_OK:
+        raise gf.GFError(rc, "gf_mlp_choose")
+    return best.value
+
+
+def evaluate(params, loops, shs, ms, sms):
+    h = shs.index(heuristic_shape(sms))
+    reg, reg_h, speed = [], [], []
+    for k, d in enumerate(loops):
+        c = choose(params, d, shs, sms)
+        best = float(ms[k].min())
+        reg.append(float(ms[k, c]) / best - 1.0)
+        reg_h.append(float(ms[k, h]) / best - 1.0)
+        speed.append(float(ms[k, h]) / float(ms[k, c]))
+    reg, reg_h, speed = map(np.array, (reg, reg_h, speed))
+    return {"mean_regret": float(reg.mean()), "p90_regret": float(np.percentile(reg, 90)),
+            "max_regret": float(reg.max()), "heuristic_mean_regret": float(reg_h.mean()),
+            "learned_vs_plain_speedup_geomean": float(np.exp(np.log(speed).mean())), "n": len(loops)}
+
+
+def run(n_loops=2000, n_train=1600, reps=2, epochs=300, out=None, log=print):
+    """Full pipeline on cuda:0; returns the evaluation dict."""
+    import torch
+    ctx = gf.Context(server_threads=4, heap_bytes=64 << 20, timeout_ns=60_000_000_000)
+    sms = ctx.grid_info("jacobi")[0]
+    shs = shapes(sms)
+    loops = config4_loops(n_loops)
+    xlen = max(d["trip"] * d["bytes"] // 8 for d in loops)
+    x = torch.empty(xlen, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+    z = torch.empty(max(d["trip"] for d in loops), dtype=torch.float64, device="cuda")
+    t0 = time.time()
+    ms = measure(ctx, loops, shs, x, z, reps=reps, log=log)
+    t_meas = time.time() - t0
+    X = np.concatenate([features(d, shs, sms) for d in loops[:n_train]])
+    y = np.log(np.maximum(ms[:n_train].reshape(-1), 1e-4))
+    params = train(X, y, epochs=epochs, log=log)
+    res = evaluate(params, loops[n_train:], shs, ms[n_train:], sms)
+    res.update({"loops": n_loops, "train": n_train, "shapes": len(shs), "reps": reps,
+                "measure_s": round(t_meas, 1), "train_rmse_log": None})
+    if out:
+        np.savez(out, ms=ms, params=params, sms=sms)
+        with open(os.path.splitext(out)[0] + ".json", "w") as f:
+            json.dump(res, f, indent=1)
+    ctx.close()
+    return res

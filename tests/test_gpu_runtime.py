@@ -95,7 +95,8 @@ def test_grid_barrier(gf_lib, ctx):
     assert ec == 0 and err.item() == 0
 
 
-def test_rpc_landing_pads(gf_lib, tmp_path):
+@pytest.mark.parametrize("bulk", [64 << 20, 1 << 20, 0])   # arena (1 and several chunks), copy-engine DMA
+def test_rpc_landing_pads(gf_lib, tmp_path, bulk):
     import torch
     gf = gf_lib
     os.environ["GF_PROBE_VAR"] = "value-42"
@@ -104,7 +105,8 @@ def test_rpc_landing_pads(gf_lib, tmp_path):
     big = torch.from_numpy(np.frombuffer(np.random.default_rng(1).bytes(nbig), dtype=np.uint8).copy()).cuda()
     ref = big.clone()
     res = torch.zeros(32, dtype=torch.int64, device="cuda")
-    with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20) as c:
+    with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20,
+                    bulk_bytes=bulk) as c:
         rc, ec = c.run("rpc_probe", [tmp_path / "small.txt", tmp_path / "big.bin", nbig], [(res, 1), (big, 1)])
     assert ec == 0
     lines = open(tmp_path / "out.txt").read().splitlines()
@@ -251,13 +253,14 @@ def test_div6_matches_ieee_division(gf_lib, ctx):
     assert np.array_equal(o[finite, 0], ref[finite])
 
 
-def test_fwrite_append_mode_in_order(gf_lib, tmp_path):
+@pytest.mark.parametrize("bulk", [64 << 20, 0])
+def test_fwrite_append_mode_in_order(gf_lib, tmp_path, bulk):
     import torch
     gf = gf_lib
-    n = (40 << 20) + 17                                          # several 16 MiB DMA chunks
+    n = (40 << 20) + 17                                          # several arena halves / DMA chunks
     data = np.frombuffer(np.random.default_rng(2).bytes(n), dtype=np.uint8).copy()
     (tmp_path / "a.bin").write_bytes(b"head")
-    with gf.Context(timeout_ns=10_000_000_000, heap_bytes=64 << 20) as c:
+    with gf.Context(timeout_ns=10_000_000_000, heap_bytes=64 << 20, bulk_bytes=bulk) as c:
         rc, ec = c.run("fwrite_modes", [tmp_path / "a.bin", n], [(torch.from_numpy(data).cuda(), 1)])
     assert ec == 0
     assert (tmp_path / "a.bin").read_bytes() == b"head" + data.tobytes() * 2

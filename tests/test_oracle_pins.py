@@ -151,3 +151,57 @@ def test_jacobi_boundary_zero_and_random_grid(oracle_bin, tmp_path):
     # max principle: the average of neighbours stays within the range of the previous sweep
     assert g.max() <= g0.max() and g.min() >= 0.0
     assert all(r > 0 for _, r in res)
+
+
+# ------------------------------------------------------------------ stress
+
+MASK = (1 << 64) - 1
+
+
+def _mix(z):
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK
+    return z ^ (z >> 31)
+
+
+def test_stress_oracle_against_memory_model(oracle_bin, tmp_path):
+    """Checksums from a word-addressed model of the three tag stores and reads
+    (a block of w words; w == 2 makes the middle and last word coincide)."""
+    T = 300
+    sizes = inputs.loguniform_int(3, 8 * T, 16, 65536).astype(np.uint32)
+    sizes[:8] = [16, 17, 23, 24, 31, 32, 65536, 40]                 # edge sizes
+    inputs.write_raw(tmp_path / "s.bin", sizes)
+    out = run([oracle_bin("stress"), str(T), tmp_path / "s.bin", tmp_path / "cs.bin"]).splitlines()
+    cs = np.fromfile(tmp_path / "cs.bin", dtype=np.uint64)
+    for t in range(T):
+        c = 0
+        for j in range(8):
+            w = int(sizes[8 * t + j]) // 8
+            h = _mix(8 * t + j + 1)
+            mem = {0: h}
+            mem[w // 2] = h ^ 0x5555555555555555
+            mem[w - 1] = (~h) & MASK
+            c ^= mem[0] ^ mem[w // 2] ^ mem[w - 1] ^ (8 * t + j)
+        assert int(cs[t]) == c
+    assert out[-1] == "fail 0"
+    want = []
+    for t in range(T):
+        h2, h3 = _mix(8 * t + 3), _mix(8 * t + 4)
+        want += ["%d %d" % (t, 0), "%d %.17g" % (t, t * 0.25 + 1.0), "%d %.6e" % (t * 1000003, float(h2) * 1e-12),
+                 "%d %x %.3f" % (t, h3 & 0xFFFFFFFF, (h3 & 0xFFFF) / 7.0)]
+    assert out[:-1] == want
+
+
+def test_loops_oracle_elementwise_and_untouched(oracle_bin, tmp_path):
+    trips = np.array([3, 0, 5], dtype=np.int64)
+    off = np.array([0, 3, 4], dtype=np.int64)             # element 3 belongs to no loop
+    a = np.array([2.0, 9.0, -0.5])
+    x = np.arange(9, dtype=np.float64)
+    y = np.ones(9)
+    z = np.full(9, -1.0)
+    for name, arr in [("t", trips), ("a", a), ("o", off), ("x", x), ("y", y), ("z", z)]:
+        inputs.write_raw(tmp_path / f"{name}.bin", arr)
+    run([oracle_bin("loops"), "3", tmp_path / "t.bin", tmp_path / "a.bin", tmp_path / "o.bin", tmp_path / "x.bin",
+         tmp_path / "y.bin", tmp_path / "z.bin", tmp_path / "zo.bin", "9"])
+    got = np.fromfile(tmp_path / "zo.bin")
+    assert got.tolist() == [1.0, 3.0, 5.0, -1.0, -1.0, -1.5, -2.0, -2.5, -3.0]
