@@ -32,6 +32,28 @@ sys.path.insert(0, ROOT)
 
 N, SWEEPS = 256, 100
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_PER_POINT = 9
+# DRAM bytes (read + write) of one full launch, scaled from an ncu capture of
+# 20 sweeps without the final write (profiles/jacobi_256_sweeps_ncu.md):
+# per sweep x 100 + the 128 MiB read of the final fwrite.  None until captured
+# for the current kernel.
+TRAFFIC_PER_LAUNCH = None
+
+
+def max_over_ranks(seconds, world, device):
+    """Replicas: the job takes as long as its slowest rank."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
 
 
 def loop_bytes(n, sweeps):
@@ -143,7 +165,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--no-write", action="store_true",
                     help="the program skips its final fwrite (profiling runs that isolate the sweeps)")
-    ap.add_argument("--workload", default="jacobi", choices=["jacobi", "stress", "batch", "learned", "serve"],
+    ap.add_argument("--workload", default="jacobi", choices=["jacobi", "stress", "batch", "learned", "serve", "e1"],
                     help="jacobi = the benchmark; the others measure the RPC/heap stress, 256-loop batching, "
                          "learned launch shapes and serving configurations")
     args = ap.parse_args()
@@ -203,13 +225,9 @@ def main():
         torch.cuda.synchronize(dev)
     barrier()
     per = [a.elapsed_time(b) / 1e3 for a, b in ev]
-    total = sum(per)
-    if world > 1:
-        t = torch.tensor([total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = t.item()
+    total = max_over_ranks(sum(per), world, dev)
     st = ctx.stats()
-    value = loop_bytes(N, sweeps) * args.steps * world / total / 1e9
+    value = job_rate(loop_bytes(N, sweeps) * args.steps, world, total) / 1e9
 
     # ---- e2e: host input staged in by the loader, result written by the program's fwrite
     e2e = None
@@ -228,6 +246,21 @@ def main():
 
     peak, peak_kind = hbm_peak()
     achieved = loop_bytes(N, sweeps) / (total / args.steps) / 1e9
+    # The sweep is bound by GB300's FP64 pipe, not HBM: 9 FP64 instructions per
+    # interior point at minimum for results bit-equal to the serial program
+    # (5 + 1 adds, and the correctly rounded /6 as 1 DMUL + 2 DFMA), and the
+    # pipe retires 2 thread-instructions per clock per SM (ncu: 16 cycles of
+    # sm__pipe_fp64_cycles_active per warp instruction).
+    sms = ctx.grid_info("jacobi")[0]
+    sm_mhz = 2070.0
+    try:
+        sm_mhz = float(json.load(open(PEAKS)).get("sm_max_mhz", sm_mhz))
+    except Exception:
+        pass
+    fp64_peak = sms * 2 * sm_mhz * 1e6 / 1e9                        # G FP64 instructions / s
+    fp64_per_launch = FP64_PER_POINT * (N - 2) ** 3 * sweeps
+    alu_achieved = fp64_per_launch / (total / args.steps) / 1e9
+    alu_sweeps = fp64_per_launch / (st.region_ns / 1e9) / 1e9 if st.region_ns else None
     cpu = None
     if rank == 0 and args.cpu_sweeps > 0:
         cv, cdt = cpu_oracle_sample(N, args.cpu_sweeps, tmp)
@@ -243,9 +276,15 @@ def main():
                                    "fused max-residual, printf per sweep, final fwrite",
                        "grid": st.grid, "block": st.block, "l2": "inputs larger than L2 (2 x 134 MB grids)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
-                         "peak_kind": peak_kind, "kernel": "program_kernel<jacobi>"},
+            "roofline": {"bound": "alu", "achieved": round(alu_achieved, 1), "peak": round(fp64_peak, 1),
+                         "unit": "G FP64 instr/s", "frac": round(alu_achieved / fp64_peak, 4),
+                         "traffic": TRAFFIC_PER_LAUNCH,
+                         "peak_kind": "derived: SMs x 2 FP64 lanes/clk x max SM clock",
+                         "kernel": "program_kernel<jacobi>",
+                         "sweeps_only": None if alu_sweeps is None else
+                         {"achieved": round(alu_sweeps, 1), "frac": round(alu_sweeps / fp64_peak, 4)},
+                         "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind}},
             "e2e": None if e2e is None else {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": N ** 3 * 8,
                     "d2h_bytes_per_step": N ** 3 * 8 + 100 * 24},
             "gpu_launches": args.steps,

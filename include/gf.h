@@ -171,6 +171,18 @@ GF_API int gf_rpc_serve(gf_ctx *ctx, const gf_serve_opts *opts);
 /* Register a host landing pad for opcode >= 256 (device: gf_rpc(opcode, ...)). */
 GF_API int gf_rpc_register(gf_ctx *ctx, uint32_t opcode, gf_host_fn fn, void *user);
 
+/* Inside a landing pad: argument k of the lane record `rec`.  *tag gets the
+ * argument kind ('i','u','l','L','d' integers and doubles, 'p' an opaque value
+ * such as FILE*, 's' string, 'b' / 'w' / 'x' a read / write / readwrite
+ * reference), *word its 8-byte value.  For references (paper Sec. 3.2,
+ * Fig. 4) the whole underlying object was copied into the record: *ptr
+ * points into that host copy at the argument's offset, *bytes is the
+ * object's size and *off the offset; write and readwrite objects are copied
+ * back to the device after the pad returns.  Any output pointer may be NULL.
+ * Returns 0, or -1 when k is out of range. */
+GF_API int gf_rec_arg(const void *rec, int k, uint8_t *tag, uint64_t *word, void **ptr, uint32_t *bytes,
+                      uint32_t *off);
+
 /* Counters of the last program waited for (see gf_stats). */
 GF_API int gf_get_stats(gf_ctx *ctx, gf_stats *out);
 
@@ -247,6 +259,28 @@ GF_API int gf_mlp_forward(const float *params, int nin, int width, int depth, co
  * milliseconds from gf_tune_features).  Writes it to *best. */
 GF_API int gf_mlp_choose(const float *params, int width, int depth, const gf_synth_loop *L, const gf_shape *shapes,
                          int nshapes, uint32_t sms, int *best);
+
+/* The k shapes with the smallest predicted times, fastest first, in idx[k]:
+ * the candidates a tuner times when it refines the model's choice with k
+ * measured runs instead of measuring every shape. */
+GF_API int gf_mlp_topk(const float *params, int width, int depth, const gf_synth_loop *L, const gf_shape *shapes,
+                       int nshapes, uint32_t sms, int k, int *idx);
+
+/* ------------------------------------------------------------------ allocator experiment */
+
+/* The paper's allocator stress (Sec. 5.1, Fig. 6): `teams` blocks of
+ * `threads` (<= 256) threads; every thread allocates `bytes` at kernel start,
+ * writes and reads its block, and frees it.  kind: 0 = the runtime's slab
+ * heap, 1 = the paper's balanced allocator (N = 32 thread slots x M = 16
+ * team slots, first chunk 4x larger), 2 = the paper's generic allocator (two
+ * lists under one lock), 3 = CUDA's device malloc (its heap limit is raised
+ * to 1 GiB on first use, which must precede any other kernel that calls
+ * malloc).  The paper's allocators use the heap arena of a borrowed program
+ * instance.  After one warm-up launch, `reps` launches are timed on `stream`;
+ * *ms = mean kernel time, *fails = NULL returns in the last launch (low 32
+ * bits) plus 2^32 x corrupted blocks.  Errors: GF_EINVAL, GF_EBUSY, GF_ECUDA. */
+GF_API int gf_alloc_e1(gf_ctx *ctx, int kind, uint32_t teams, uint32_t threads, uint32_t bytes, int reps,
+                       void *stream, float *ms, uint64_t *fails);
 
 /* Number of SMs and resident blocks per SM that a program's grid uses at
  * `block` threads (for sizing, tests and roofline accounting). */

@@ -24,10 +24,11 @@ NVFLAGS = ARCH + INC + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcom
 CXXFLAGS = INC + ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-Wall"]
 
 CU = ["runtime.cu", "noalloc.cu", "programs/legacy.cu", "programs/probes.cu", "programs/stress.cu", "programs/batch.cu",
-      "programs/synth.cu", "programs/serve.cu"]
+      "programs/synth.cu", "programs/serve.cu",
+      "programs/alloc_e1.cu", "programs/libc.cu"]
 CPP = ["host/server.cpp", "host/mlp.cpp"]
 HEADERS = ["gf_layout.h", "gf_device.cuh", "gf_device_rpc.cuh", "gf_device_heap.cuh", "gf_program.h",
-           "host/server.h", "gf_errors.h", "gf_internal.h", "gf_fastdiv.cuh"]
+           "host/server.h", "gf_errors.h", "gf_internal.h", "gf_fastdiv.cuh", "gf_paper_alloc.cuh", "gf_device_libc.cuh"]
 
 
 def _newer(obj, deps):

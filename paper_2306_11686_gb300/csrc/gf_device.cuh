@@ -680,8 +680,10 @@ namespace gfd {
 
 typedef int (*main_t)(int, char **);
 
-template <main_t MAIN>
-__global__ void __launch_bounds__(GF_BLOCK, GF_MIN_BLOCKS) program_kernel(gf_state *S, int argc, char **argv)
+/* MINB: resident blocks per SM the kernel is compiled for (a register cap);
+ * memory-bound programs ask for more resident warps with GF_MAIN_BOUNDS. */
+template <main_t MAIN, int MINB = GF_MIN_BLOCKS>
+__global__ void __launch_bounds__(GF_BLOCK, MINB) program_kernel(gf_state *S, int argc, char **argv)
 {
     if (threadIdx.x == 0)
         s_st = S;
@@ -707,22 +709,25 @@ __global__ void __launch_bounds__(GF_BLOCK, GF_MIN_BLOCKS) program_kernel(gf_sta
 /* host-side registration of a program (name -> cooperative launcher) */
 #include "gf_program.h"
 
-#define GF_MAIN(name)                                                                          \
+#define GF_MAIN_BOUNDS(name, minb)                                                             \
     __device__ int gf_main_##name(int argc, char **argv);                                     \
     static cudaError_t gf_launch_##name(void **args, unsigned grid, unsigned block, void *stream) \
     {                                                                                          \
-        return cudaLaunchCooperativeKernel((const void *)&gfd::program_kernel<gf_main_##name>, \
+        return cudaLaunchCooperativeKernel((const void *)&gfd::program_kernel<gf_main_##name, minb>, \
                                            dim3(grid), dim3(block), args, 0, (cudaStream_t)stream); \
     }                                                                                          \
     static int gf_occ_##name(unsigned block)                                                   \
     {                                                                                          \
         int n = 0;                                                                             \
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                     \
-                &n, (const void *)&gfd::program_kernel<gf_main_##name>, (int)block, 0) != cudaSuccess) \
+                &n, (const void *)&gfd::program_kernel<gf_main_##name, minb>, (int)block, 0) != cudaSuccess) \
             return -1;                                                                         \
         return n;                                                                              \
     }                                                                                          \
     static const int gf_reg_##name = gf_program_register(#name, gf_launch_##name, gf_occ_##name); \
     __device__ int gf_main_##name
+
+/* GF_MAIN(name)(int argc, char **argv) { ... } defines and registers a program */
+#define GF_MAIN(name) GF_MAIN_BOUNDS(name, GF_MIN_BLOCKS)
 
 #endif

@@ -44,11 +44,14 @@ struct argpack {
             n++;
         }
     }
-    __device__ void blob(char t, const void *p, uint32_t bytes)
+    /* p = start of the underlying object, bytes = its size, off = the
+     * argument pointer's offset inside it (paper Fig. 4c: addRefArg(ptr,
+     * mode, size, offset)) */
+    __device__ void blob(char t, const void *p, uint32_t bytes, uint32_t off = 0)
     {
         if (n < GF_MAX_ARGS) {
             tag[n] = t;
-            word[n] = ((uint64_t)bytes << 32) | tail;   /* offset in tail | bytes */
+            word[n] = ((uint64_t)bytes << 32) | ((uint64_t)(off & 0xffffu) << 16) | tail;   /* bytes | off | tail */
             src[n] = p;
             len[n] = bytes;
             tail += (bytes + 7u) & ~7u;
@@ -66,9 +69,10 @@ struct argpack {
 };
 
 /* reference-argument wrappers (paper Fig. 4: addRefArg(ptr, mode, size, offset)) */
-struct ref_r { const void *p; uint32_t bytes; };
-struct ref_w { void *p; uint32_t bytes; };
-struct ref_rw { void *p; uint32_t bytes; };
+struct ref_r { const void *p; uint32_t bytes, off; };
+struct ref_w { void *p; uint32_t bytes, off; };
+struct ref_rw { void *p; uint32_t bytes, off; };
+struct ref_val { uint64_t v; };                 /* a pointer passed as a plain value */
 struct dma_ref { uint64_t addr; uint64_t bytes; };
 
 __device__ inline void pack1(argpack &a, int v) { a.val(GF_T_I32, (uint64_t)(int64_t)v); }
@@ -90,9 +94,10 @@ __device__ inline void pack1(argpack &a, const char *s)
 __device__ inline void pack1(argpack &a, char *s) { pack1(a, (const char *)s); }
 __device__ inline void pack1(argpack &a, const void *p) { a.val(GF_T_PTR, (uint64_t)p); }
 __device__ inline void pack1(argpack &a, void *p) { a.val(GF_T_PTR, (uint64_t)p); }
-__device__ inline void pack1(argpack &a, ref_r r) { a.blob(GF_T_BLOB_R, r.p, r.bytes); }
-__device__ inline void pack1(argpack &a, ref_w r) { a.blob(GF_T_BLOB_W, r.p, r.bytes); }
-__device__ inline void pack1(argpack &a, ref_rw r) { a.blob(GF_T_BLOB_RW, r.p, r.bytes); }
+__device__ inline void pack1(argpack &a, ref_r r) { a.blob(GF_T_BLOB_R, r.p, r.bytes, r.off); }
+__device__ inline void pack1(argpack &a, ref_w r) { a.blob(GF_T_BLOB_W, r.p, r.bytes, r.off); }
+__device__ inline void pack1(argpack &a, ref_rw r) { a.blob(GF_T_BLOB_RW, r.p, r.bytes, r.off); }
+__device__ inline void pack1(argpack &a, ref_val r) { a.val(GF_T_PTR, r.v); }
 __device__ inline void pack1(argpack &a, dma_ref r)
 {
     a.val(GF_T_DMA, r.addr);
@@ -158,7 +163,7 @@ __device__ inline void write_rec(uint8_t *dst, const argpack &a, uint32_t lane, 
         w[k++] = a.word[t];
     for (uint32_t t = 0; t < a.n; t++)
         if (a.src[t] && a.tag[t] != GF_T_BLOB_W)
-            copy_out(w + k + (uint32_t)(a.word[t] & 0xffffffffu) / 8, a.src[t], a.len[t]);
+            copy_out(w + k + (uint32_t)(a.word[t] & 0xffffu) / 8, a.src[t], a.len[t]);
 }
 
 /* fmt cache: open addressing over device-address keys of shipped formats */
@@ -336,7 +341,7 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
             const uint64_t *tail = rw + 2 + ntag / 8 + a.n;
             for (uint32_t k = 0; k < a.n; k++)
                 if (a.tag[k] == GF_T_BLOB_W || a.tag[k] == GF_T_BLOB_RW)
-                    copy_back((void *)a.src[k], tail + (uint32_t)(a.word[k] & 0xffffffffu) / 8, a.len[k]);
+                    copy_back((void *)a.src[k], tail + (uint32_t)(a.word[k] & 0xffffu) / 8, a.len[k]);
         } else if (mine) {
             st = wst;
             ret = -1;
@@ -594,8 +599,82 @@ template <class... A> __device__ inline int64_t gf_rpc(uint32_t opcode, int *sta
 {
     return gfd::rpc(opcode, nullptr, status, args...);
 }
-__device__ inline gfd::ref_r gf_ref_read(const void *p, uint32_t bytes) { return gfd::ref_r{p, bytes}; }
-__device__ inline gfd::ref_w gf_ref_write(void *p, uint32_t bytes) { return gfd::ref_w{p, bytes}; }
-__device__ inline gfd::ref_rw gf_ref_readwrite(void *p, uint32_t bytes) { return gfd::ref_rw{p, bytes}; }
+/* Reference arguments (paper Sec. 3.2, Fig. 4c): the whole underlying
+ * object [obj, obj + bytes) travels to the host, and the host callee gets a
+ * pointer at offset `off` into its copy.  read: copied to the host only;
+ * write: copied back only; readwrite: both.  Inline objects are limited by
+ * the slot size (and offsets to 64 KiB). */
+__device__ inline gfd::ref_r gf_ref_read(const void *obj, uint32_t bytes, uint32_t off = 0)
+{
+    return gfd::ref_r{obj, bytes, off};
+}
+__device__ inline gfd::ref_w gf_ref_write(void *obj, uint32_t bytes, uint32_t off = 0)
+{
+    return gfd::ref_w{obj, bytes, off};
+}
+__device__ inline gfd::ref_rw gf_ref_readwrite(void *obj, uint32_t bytes, uint32_t off = 0)
+{
+    return gfd::ref_rw{obj, bytes, off};
+}
+
+/* Underlying object of a pointer that no analysis could pin down (the
+ * paper's _FindObj, Sec. 3.2): the device heap's slab metadata and page
+ * table give the enclosing block.  Returns false for memory the heap did not
+ * hand out (the pointer then travels as a plain value, as in the paper). */
+__device__ inline bool gf_find_obj(const void *p, uint64_t *base, uint64_t *size)
+{
+    gf_heap *H = &gfd::s_st->heap;
+    const uint64_t a = (uint64_t)p;
+    if (a >= H->slab_base && a < H->slab_base + H->slab_bytes) {
+        const uint32_t s = (uint32_t)((a - H->slab_base) >> GF_SLAB_SHIFT);
+        const uint32_t c1 = *(volatile uint32_t *)&((uint32_t *)H->slab_meta)[4 * s];
+        if (!c1)
+            return false;
+        const uint64_t bs = 16ull << (c1 - 1);
+        *base = H->slab_base + ((a - H->slab_base) / bs) * bs;
+        *size = bs;
+        return true;
+    }
+    if (a >= H->large_base && a < H->large_base + H->large_bytes) {
+        const volatile uint32_t *sz = (const volatile uint32_t *)H->large_size;
+        int64_t pg = (int64_t)((a - H->large_base) >> GF_PAGE_SHIFT);
+        for (int64_t k = pg; k >= 0 && pg - k < 4096; k--)      /* bounded backward scan */
+            if (sz[k]) {
+                if ((uint64_t)(pg - k) < sz[k]) {
+                    *base = H->large_base + ((uint64_t)k << GF_PAGE_SHIFT);
+                    *size = (uint64_t)sz[k] << GF_PAGE_SHIFT;
+                    return true;
+                }
+                return false;
+            }
+    }
+    return false;
+}
+
+/* A reference argument whose object is found at run time (readwrite), or a
+ * plain value when it is not a heap block or too large to travel inline. */
+struct gf_ref_any {
+    bool found;
+    gfd::ref_rw r;
+    uint64_t v;
+};
+__device__ inline gf_ref_any gf_ref_lookup(void *p)
+{
+    uint64_t base = 0, size = 0;
+    gf_ref_any x;
+    x.v = (uint64_t)p;
+    x.found = gf_find_obj(p, &base, &size) && size <= GF_INLINE_BLOB_MAX;
+    x.r = gfd::ref_rw{(void *)base, (uint32_t)size, (uint32_t)((uint64_t)p - base)};
+    return x;
+}
+namespace gfd {
+__device__ inline void pack1(argpack &a, gf_ref_any x)
+{
+    if (x.found)
+        pack1(a, x.r);
+    else
+        a.val(GF_T_PTR, x.v);
+}
+} // namespace gfd
 
 #endif

@@ -36,7 +36,7 @@ __device__ __forceinline__ double gf_div6_rn(double x)
     if (e - 23u > 2000u)                             /* outside [2^-1000, 2^1001): IEEE path */
         return gf_div6_ieee(x);
     const double q = __dmul_rn(x, r);
-    const double rho = __fma_rn(-q, 6.0, x);
+    const double rho = __fma_rn(q, -6.0, x);        /* x - 6q, exact; the sign sits on the constant */
     return __fma_rn(rho, r, q);
 }
 

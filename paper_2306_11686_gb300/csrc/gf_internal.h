@@ -14,4 +14,6 @@ void gf_inst_release(gf_ctx *c, int idx);
 /* device scratch of the instance (its reduction-partials array, >= 16 KiB) */
 void *gf_inst_scratch(gf_ctx *c, int idx);
 int gf_ctx_server_threads(gf_ctx *c);
+/* the instance's heap arena (device) and its size */
+void gf_inst_heap(gf_ctx *c, int idx, void **base, uint64_t *bytes);
 #endif

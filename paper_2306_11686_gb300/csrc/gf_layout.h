@@ -39,6 +39,7 @@ enum gf_opcode {
     GF_OP_GETENV = 6,     /* (name) -> device-readable interned copy, 0 if unset          */
     GF_OP_FREAD = 7,      /* (buf, size, nmemb, FILE*) -> items read, bytes written back  */
     GF_OP_FFLUSH = 8,     /* (FILE*) -> 0 / EOF                                           */
+    GF_OP_STRTOD = 9,     /* (str, int64 *used) -> bits of strtod(str), chars consumed    */
     GF_OP_USER = 256      /* first opcode for handlers registered with gf_rpc_register    */
 };
 
@@ -178,6 +179,7 @@ typedef struct gf_state {
     uint64_t st_region_ns;        /* initial thread: publish -> all blocks done       */
     uint64_t t_main_start, t_main_end;
     uint64_t lat_hist[GF_LAT_BUCKETS];  /* RPC round trips (claim -> host done), lane records */
+    uint32_t rand_words[40];      /* rand() state of the program (device libc)        */
     gf_heap heap;
 } gf_state;
 

@@ -10,6 +10,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "gf.h"
@@ -62,10 +63,10 @@ extern "C" GF_API int gf_mlp_forward(const float *P, int nin, int width, int dep
     return GF_OK;
 }
 
-extern "C" GF_API int gf_mlp_choose(const float *P, int width, int depth, const gf_synth_loop *L,
-                                    const gf_shape *shapes, int nshapes, uint32_t sms, int *best)
+extern "C" GF_API int gf_mlp_topk(const float *P, int width, int depth, const gf_synth_loop *L,
+                                  const gf_shape *shapes, int nshapes, uint32_t sms, int k, int *idx)
 {
-    if (!P || !L || !shapes || nshapes < 1 || !best)
+    if (!P || !L || !shapes || nshapes < 1 || !idx || k < 1 || k > nshapes)
         return GF_EINVAL;
     std::vector<float> f((size_t)nshapes * GF_TUNE_NFEAT), y((size_t)nshapes);
     for (int s = 0; s < nshapes; s++)
@@ -73,10 +74,18 @@ extern "C" GF_API int gf_mlp_choose(const float *P, int width, int depth, const 
     int rc = gf_mlp_forward(P, GF_TUNE_NFEAT, width, depth, f.data(), nshapes, y.data());
     if (rc)
         return rc;
-    int b = 0;
-    for (int s = 1; s < nshapes; s++)
-        if (y[(size_t)s] < y[(size_t)b])
-            b = s;
-    *best = b;
+    std::vector<int> order((size_t)nshapes);
+    for (int s = 0; s < nshapes; s++)
+        order[(size_t)s] = s;
+    std::partial_sort(order.begin(), order.begin() + k, order.end(),
+                      [&](int a, int b) { return y[(size_t)a] < y[(size_t)b] || (y[(size_t)a] == y[(size_t)b] && a < b); });
+    for (int j = 0; j < k; j++)
+        idx[j] = order[(size_t)j];
     return GF_OK;
+}
+
+extern "C" GF_API int gf_mlp_choose(const float *P, int width, int depth, const gf_synth_loop *L,
+                                    const gf_shape *shapes, int nshapes, uint32_t sms, int *best)
+{
+    return gf_mlp_topk(P, width, depth, L, shapes, nshapes, sms, 1, best);
 }

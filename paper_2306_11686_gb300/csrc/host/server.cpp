@@ -4,8 +4,12 @@
 #include <fcntl.h>
 #include <stdlib.h>
 #include <string.h>
+#include <sys/mman.h>
+#include <sys/stat.h>
 #include <time.h>
 #include <unistd.h>
+
+#include <thread>
 #include <chrono>
 #include <vector>
 
@@ -41,6 +45,96 @@ RecView::RecView(const uint8_t *r) : base(r)
     tags = r + sizeof(gf_rec_hdr);
     words = (const uint64_t *)(tags + ((nargs + 7u) & ~7u));
     tail = (const uint8_t *)(words + nargs);
+}
+
+/*
+ * fwrite of a large buffer.  A single write(2) to one file copies into the
+ * page cache on one thread (the kernel serialises writers of a file), which
+ * is the bottleneck for a 128 MiB write.  For a regular file not opened for
+ * append, the target range is mapped instead and several threads copy into
+ * it (page faults of different pages proceed in parallel); the stdio
+ * position is then moved past the data.  The bytes in the file are the same;
+ * anything that is not a plain regular file, and small writes, use fwrite.
+ */
+static size_t big_fwrite(const void *src, size_t size, size_t nmemb, FILE *f)
+{
+    const uint64_t n = (uint64_t)size * nmemb;
+    const uint64_t min_par = 8ull << 20;
+    if (n < min_par)
+        return fwrite(src, size, nmemb, f);
+    if (fflush(f) != 0)
+        return 0;
+    const int fd = fileno(f);
+    struct stat sb;
+    const off_t pos = ftello(f);
+    const int fl = fd >= 0 ? fcntl(fd, F_GETFL) : -1;
+    const bool writable = fl >= 0 && ((fl & O_ACCMODE) == O_WRONLY || (fl & O_ACCMODE) == O_RDWR);
+    if (fd < 0 || pos < 0 || !writable || (fl & O_APPEND) || fstat(fd, &sb) != 0 || !S_ISREG(sb.st_mode) ||
+        lseek(fd, 0, SEEK_CUR) != pos)
+        return fwrite(src, size, nmemb, f);
+    /* a shared writable mapping needs a descriptor opened for reading too:
+     * reopen the same file read-write through /proc (fall back if refused) */
+    char path[64];
+    snprintf(path, sizeof path, "/proc/self/fd/%d", fd);
+    const int rfd = open(path, O_RDWR);
+    if (rfd < 0)
+        return fwrite(src, size, nmemb, f);
+    const off_t end = pos + (off_t)n;
+    if (end > sb.st_size && ftruncate(rfd, end) != 0) {
+        close(rfd);
+        return fwrite(src, size, nmemb, f);
+    }
+    const long pg = sysconf(_SC_PAGESIZE);
+    const off_t mstart = pos / pg * pg;
+    const size_t mlen = (size_t)(end - mstart);
+    void *m = mmap(nullptr, mlen, PROT_WRITE | PROT_READ, MAP_SHARED, rfd, mstart);
+    if (m == MAP_FAILED) {
+        const int bad = end > sb.st_size && ftruncate(rfd, sb.st_size) != 0;
+        close(rfd);
+        return bad ? 0 : fwrite(src, size, nmemb, f);
+    }
+    unsigned char *dst = (unsigned char *)m + (pos - mstart);
+    const unsigned nthr = 8;
+    const uint64_t part = ((n + nthr - 1) / nthr + 4095) & ~4095ull;
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nthr; t++) {
+        const uint64_t lo = t * part;
+        if (lo >= n)
+            break;
+        const uint64_t len = n - lo < part ? n - lo : part;
+        th.emplace_back([=] { memcpy(dst + lo, (const unsigned char *)src + lo, len); });
+    }
+    for (auto &x : th)
+        x.join();
+    munmap(m, mlen);
+    close(rfd);
+    if (fseeko(f, end, SEEK_SET) != 0)
+        return 0;
+    return nmemb;
+}
+
+/* Argument k of a lane record, for user landing pads (include/gf.h). */
+extern "C" __attribute__((visibility("default"))) int gf_rec_arg(const void *rec, int k, uint8_t *tag, uint64_t *word,
+                                                                   void **ptr, uint32_t *bytes, uint32_t *off)
+{
+    if (!rec)
+        return -1;
+    RecView r((const uint8_t *)rec);
+    if (k < 0 || (uint32_t)k >= r.nargs)
+        return -1;
+    const uint8_t t = r.tag((uint32_t)k);
+    if (tag)
+        *tag = t;
+    if (word)
+        *word = r.word((uint32_t)k);
+    const bool ref = t == GF_T_STR || t == GF_T_BLOB_R || t == GF_T_BLOB_W || t == GF_T_BLOB_RW;
+    if (ptr)
+        *ptr = ref ? (void *)(r.blob((uint32_t)k) + r.ptr_off((uint32_t)k)) : nullptr;
+    if (bytes)
+        *bytes = ref ? r.blob_len((uint32_t)k) : 8;
+    if (off)
+        *off = ref ? r.ptr_off((uint32_t)k) : 0;
+    return 0;
 }
 
 Server::Server() {}
@@ -328,7 +422,7 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
             if (!seg || !seg->bulk || off + len > seg->bulk_bytes || len < bytes)
                 return 0;
             std::lock_guard<std::mutex> g(out_mu_);
-            const size_t k = op == GF_OP_FWRITE ? fwrite(seg->bulk + off, size, nmemb, f)
+            const size_t k = op == GF_OP_FWRITE ? big_fwrite(seg->bulk + off, size, nmemb, f)
                                                 : fread(seg->bulk + off, size, nmemb, f);
             stats.dma_bytes += k * size;
             return (int64_t)k;
@@ -360,6 +454,19 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
     }
     case GF_OP_CLOCK:
         return (int64_t)clock();
+    case GF_OP_STRTOD: {
+        /* the device's slow path: exact conversion by the host libc */
+        if (r.nargs < 2 || r.tag(0) != GF_T_STR || r.tag(1) != GF_T_BLOB_W || r.blob_len(1) < 8)
+            return 0;
+        const char *s = r.str(0);
+        char *end = nullptr;
+        const double v = strtod(s, &end);
+        const int64_t used = (int64_t)(end - s);
+        memcpy(r.blob(1), &used, 8);
+        int64_t bits;
+        memcpy(&bits, &v, 8);
+        return bits;
+    }
     case GF_OP_GETENV: {
         if (r.nargs < 1 || r.tag(0) != GF_T_STR || !intern_)
             return 0;

@@ -123,9 +123,11 @@ struct RecView {
     explicit RecView(const uint8_t *r);
     uint8_t tag(uint32_t k) const { return tags[k]; }
     uint64_t word(uint32_t k) const { return words[k]; }
-    const char *str(uint32_t k) const { return (const char *)(tail + (uint32_t)(words[k] & 0xffffffffu)); }
+    /* reference arguments: word = object bytes << 32 | pointer offset << 16 | tail offset */
+    const char *str(uint32_t k) const { return (const char *)(tail + (uint32_t)(words[k] & 0xffffu)); }
     uint32_t blob_len(uint32_t k) const { return (uint32_t)(words[k] >> 32); }
-    uint8_t *blob(uint32_t k) const { return (uint8_t *)(tail + (uint32_t)(words[k] & 0xffffffffu)); }
+    uint32_t ptr_off(uint32_t k) const { return (uint32_t)((words[k] >> 16) & 0xffffu); }
+    uint8_t *blob(uint32_t k) const { return (uint8_t *)(tail + (uint32_t)(words[k] & 0xffffu)); }
 };
 
 } // namespace gfh

@@ -17,7 +17,9 @@
 
 /* loops mode n chunk sched         buffers: 0 = int64 trips[n], 1 = double a[n], 2 = int64 off[n],
  *                                  3 = double x[], 4 = double y[], 5 = double z[], 6 = int64 prefix[n+1] */
-GF_MAIN(loops)(int argc, char **argv)
+/* memory-bound: compiled for 8 resident blocks per SM (2048 threads) so more
+ * loads are in flight; its serial part makes no RPC, so little spills */
+GF_MAIN_BOUNDS(loops, 8)(int argc, char **argv)
 {
     if (argc < 5)
         return 2;

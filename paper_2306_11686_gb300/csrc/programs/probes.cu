@@ -279,3 +279,57 @@ GF_MAIN(fwrite_modes)(int argc, char **argv)
     gf_fclose(f);
     return w == 2 * n ? 0 : 4;
 }
+
+/*
+ * fig4_probe opcode               buffer 0 = int64 out[8]
+ * The call site of the paper's worked example (Fig. 4),
+ *     r = fscanf(fd, "%f %i %i", &s.f, s.a ? &i : &s.b, p);
+ * issued to a user landing pad: fd by value (an opaque FILE*), the format as a
+ * read-only reference, &s.f readwrite with the whole struct at offset
+ * offsetof(f), &i write-only (s.a != 0), and p -- an interior pointer no
+ * analysis pins down -- looked up in the device heap at run time.
+ */
+struct fig4_S {
+    int a, b;
+    float f;
+};
+GF_MAIN(fig4_probe)(int argc, char **argv)
+{
+    if (argc < 2)
+        return 2;
+    const unsigned op = (unsigned)gf_atoll(argv[1]);
+    long long *out = (long long *)gf_buffer(0);
+    fig4_S s;
+    s.a = 1;
+    s.b = 2;
+    s.f = 0.5f;
+    int i = -1;
+    int *blk = (int *)gf_malloc(16);
+    if (!blk || !out)
+        return 3;
+    blk[0] = 10;
+    blk[1] = 11;
+    blk[2] = 12;
+    blk[3] = 13;
+    int *p = blk + 1;
+    const char *fmt = "%f %i %i";
+    const unsigned long long fd = 0xF11E0ull;
+    int st = 0;
+    long long r;
+    if (s.a)
+        r = gf_rpc(op, &st, fd, gf_ref_read(fmt, 9, 0), gf_ref_readwrite(&s, sizeof(fig4_S), offsetof(fig4_S, f)),
+                   gf_ref_write(&i, sizeof(int), 0), gf_ref_lookup(p));
+    else
+        r = gf_rpc(op, &st, fd, gf_ref_read(fmt, 9, 0), gf_ref_readwrite(&s, sizeof(fig4_S), offsetof(fig4_S, f)),
+                   gf_ref_readwrite(&s, sizeof(fig4_S), offsetof(fig4_S, b)), gf_ref_lookup(p));
+    out[0] = r;
+    out[1] = st;
+    out[2] = __float_as_int(s.f);
+    out[3] = s.a;
+    out[4] = s.b;
+    out[5] = i;
+    out[6] = blk[1];
+    out[7] = blk[0] + 100 * blk[2] + 10000 * blk[3];
+    gf_free(blk);
+    return 0;
+}

@@ -411,7 +411,8 @@ extern "C" GF_API int gf_init(const gf_config *cfg, gf_ctx **out)
     gf_config_default(&cf);
     if (cfg)
         cf = *cfg;
-    if (!pow2(cf.ring_slots) || cf.slot_bytes < 1024 || cf.slot_bytes % 64 || !pow2(cf.fmt_cache) ||
+    if (!pow2(cf.ring_slots) || cf.slot_bytes < 1024 || cf.slot_bytes > 65536 || cf.slot_bytes % 64 ||
+        !pow2(cf.fmt_cache) ||
         cf.max_programs < 1 || cf.max_programs > 1024 || cf.heap_small_pct > 100 || cf.timeout_ns <= 0)
         return GF_EINVAL;
     if (cf.server_threads && (!pow2(cf.server_threads) || cf.server_threads > cf.ring_slots))
@@ -747,6 +748,12 @@ void gf_inst_release(gf_ctx *c, int idx)
 
 int gf_ctx_server_threads(gf_ctx *c) { return (int)c->cfg.server_threads; }
 void *gf_inst_scratch(gf_ctx *c, int idx) { return c->inst[(size_t)idx]->d_partials; }
+void gf_inst_heap(gf_ctx *c, int idx, void **base, uint64_t *bytes)
+{
+    Instance *in = c->inst[(size_t)idx];
+    *base = in->d_heap;
+    *bytes = in->slab_bytes + in->large_bytes;
+}
 
 extern "C" GF_API int gf_done(gf_handle *h)
 {

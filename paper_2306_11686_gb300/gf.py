@@ -127,6 +127,14 @@ _sig = {
     "gf_mlp_choose": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(gf_synth_loop),
                                      ctypes.POINTER(gf_shape), ctypes.c_int, ctypes.c_uint32,
                                      ctypes.POINTER(ctypes.c_int)]),
+    "gf_rec_arg": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_uint64),
+                                  ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_uint32),
+                                  ctypes.POINTER(ctypes.c_uint32)]),
+    "gf_alloc_e1": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
+                                   _P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)]),
+    "gf_mlp_topk": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(gf_synth_loop),
+                                   ctypes.POINTER(gf_shape), ctypes.c_int, ctypes.c_uint32, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int)]),
     "gf_axpy_batch_graph": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P,
                                            ctypes.POINTER(ctypes.c_float)]),
 }

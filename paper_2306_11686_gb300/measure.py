@@ -111,7 +111,8 @@ def learned(args):
     from . import tune
     res = tune.run(n_loops=2000, n_train=1600, reps=2, epochs=300, log=lambda m: print("#", m, flush=True),
                    out=os.path.join(args.out_dir or ".", "learned_ds.npz") if args.out_dir else None)
-    line = {"metric": "learned vs plain config", "value": round(res["mean_regret"], 4), "unit": "mean regret",
+    line = {"metric": "learned vs plain config", "value": round(res["retimed"]["refined"]["mean"], 4),
+            "unit": "mean regret (model top-3, re-timed vs autotuner)",
             "n_gpus": 1, "higher_is_better": False, "dtype": "fp32 model", "data": "synthetic",
             "config": {"workload": "2000 synthetic loops (1600 train / 400 held out), 96 launch shapes"},
             "detail": res}
@@ -142,5 +143,37 @@ def serve_run(args):
     shutil.rmtree(tmp, ignore_errors=True)
 
 
+def e1(args):
+    """The paper's allocator grid (Sec. 5.1, Fig. 6): teams x threads/team in
+    {1, 32, 64, 128, 256}^2, one 64 B allocate/use/free per thread, for the
+    slab heap, the paper's balanced and generic allocators, and CUDA malloc."""
+    import ctypes
+    kinds = {0: "slab", 1: "balanced", 2: "generic", 3: "cuda_malloc"}
+    sizes = (1, 32, 64, 128, 256)
+    table = {}
+    with gf.Context(heap_bytes=1 << 30, timeout_ns=int(60e9)) as ctx:
+        for k, name in kinds.items():
+            for teams in sizes:
+                for threads in sizes:
+                    ms, fails = ctypes.c_float(), ctypes.c_uint64()
+                    rc = gf.gf_alloc_e1(ctx.h, k, teams, threads, 64, 5, None, ctypes.byref(ms),
+                                        ctypes.byref(fails))
+                    if rc:
+                        raise gf.GFError(rc, f"gf_alloc_e1({name}, {teams}, {threads})")
+                    table[f"{name}/{teams}x{threads}"] = {"s": ms.value / 1e3, "fails": int(fails.value)}
+    big = lambda n: table[f"{n}/256x256"]["s"]
+    line = {"metric": "allocator alloc/free pairs/s", "value": round(65536 / big("slab")), "unit": "pairs/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "bytes", "data": "synthetic",
+            "config": {"workload": "paper Fig. 6 grid: teams x threads in {1,32,64,128,256}^2, 64 B per thread"},
+            "detail": {"seconds": table,
+                       "speedup_vs_cuda_malloc_256x256": big("cuda_malloc") / big("slab"),
+                       "speedup_vs_balanced_256x256": big("balanced") / big("slab"),
+                       "balanced_vs_cuda_malloc_256x256": big("cuda_malloc") / big("balanced"),
+                       "balanced_vs_cuda_malloc_1x1": table["cuda_malloc/1x1"]["s"] / table["balanced/1x1"]["s"],
+                       "balanced_vs_cuda_malloc_256x32": table["cuda_malloc/256x32"]["s"]
+                       / table["balanced/256x32"]["s"]}}
+    print(json.dumps(line))
+
+
 def run(args):
-    {"stress": stress, "batch": batch, "learned": learned, "serve": serve_run}[args.workload](args)
+    {"stress": stress, "batch": batch, "learned": learned, "serve": serve_run, "e1": e1}[args.workload](args)

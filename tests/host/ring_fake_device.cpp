@@ -67,6 +67,61 @@ static uint32_t put_rec(uint8_t *dst, uint32_t lane, int a, int b)
     return bytes;
 }
 
+/* a general lane record: value words and string / blob tails in the device layout */
+struct Arg {
+    char tag;
+    uint64_t word;
+    std::string bytes;     /* for 's' (with NUL) and 'b' */
+};
+static uint32_t put_args(uint8_t *dst, const std::vector<Arg> &args)
+{
+    const uint32_t n = (uint32_t)args.size();
+    uint32_t tail = 0;
+    std::vector<uint64_t> words(n);
+    for (uint32_t k = 0; k < n; k++) {
+        words[k] = args[k].word;
+        if (args[k].tag == 's' || args[k].tag == 'b') {
+            words[k] = ((uint64_t)args[k].bytes.size() << 32) | tail;
+            tail += ((uint32_t)args[k].bytes.size() + 7u) & ~7u;
+        }
+    }
+    const uint32_t bytes = 16 + ((n + 7u) & ~7u) + 8 * n + tail;
+    memset(dst, 0, bytes);
+    uint64_t *w = (uint64_t *)dst;
+    w[0] = (uint64_t)bytes | ((uint64_t)n << 32);
+    for (uint32_t k = 0; k < n; k++)
+        dst[16 + k] = (uint8_t)args[k].tag;
+    uint64_t *wd = (uint64_t *)(dst + 16 + ((n + 7u) & ~7u));
+    uint8_t *tl = (uint8_t *)(wd + n);
+    for (uint32_t k = 0; k < n; k++) {
+        wd[k] = words[k];
+        if (args[k].tag == 's' || args[k].tag == 'b')
+            memcpy(tl + (words[k] & 0xffff), args[k].bytes.data(), args[k].bytes.size());
+    }
+    return bytes;
+}
+
+/* one synchronous single-lane call of opcode op */
+static int64_t call1(Ring &R, uint32_t op, const std::vector<Arg> &args)
+{
+    const uint64_t t = R.ticket.fetch_add(1);
+    gf_slot_hdr *h = R.hdr(t);
+    while (acq(&h->seq) != t)
+        std::this_thread::yield();
+    put_args((uint8_t *)h + GF_SLOT_PAYLOAD_OFF, args);
+    h->opcode = op;
+    h->nlanes = 1;
+    h->flags = 0;
+    h->fmt_len = 0;
+    h->fmt_key = 0;
+    rel(&h->seq, t + 1);
+    while (acq(&h->seq) != t + 2)
+        std::this_thread::yield();
+    const int64_t r = *(int64_t *)((uint8_t *)h + GF_SLOT_RET_OFF);
+    rel(&h->seq, t + R.nslots);
+    return r;
+}
+
 static const char *FMT = "p %d s %d\n";
 static const uint64_t FMT_KEY = 0x1000;
 
@@ -308,6 +363,46 @@ int main(int argc, char **argv)
         for (int s = 2; s < 10; s++)
             if (call(R, 1, {s}, r, true, 5.0))
                 return fail("no recovery");
+        S.join();
+        fclose(out);
+    } else if (sc == "bulkfile") {
+        /* large fwrite from the bulk arena (the parallel page-cache path for
+         * regular files, plain fwrite for append mode) after a small inline one */
+        const uint64_t len = (40ull << 20) + 3;
+        std::vector<uint8_t> arena(len);
+        for (uint64_t k = 0; k < len; k++)
+            arena[k] = (uint8_t)((k * 2654435761ull) >> 13);
+        R.seg.bulk = arena.data();
+        R.seg.bulk_bytes = len;
+        const std::string path = std::string(argv[2]) + ".bin";
+        for (const char *mode : {"wb", "w+b", "ab"}) {
+            if (!strcmp(mode, "ab")) {
+                FILE *pre = fopen(path.c_str(), "wb");
+                fwrite("PRE", 1, 3, pre);
+                fclose(pre);
+            }
+            const int64_t fh = call1(R, GF_OP_FOPEN, {{'s', 0, path + '\0'}, {'s', 0, std::string(mode) + '\0'}});
+            if (!fh)
+                return fail("fopen");
+            if (call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', 4, ""}, {'L', (uint64_t)fh, ""}, {'b', 0, "HEAD"}}) != 4)
+                return fail("inline fwrite");
+            if (call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', len, ""}, {'L', (uint64_t)fh, ""}, {'A', 0, ""},
+                                        {'L', len, ""}}) != (int64_t)len)
+                return fail("arena fwrite");
+            if (call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', 4, ""}, {'L', (uint64_t)fh, ""}, {'b', 0, "TAIL"}}) != 4)
+                return fail("inline fwrite after");
+            if (call1(R, GF_OP_FCLOSE, {{'L', (uint64_t)fh, ""}}) != 0)
+                return fail("fclose");
+            FILE *in = fopen(path.c_str(), "rb");
+            std::vector<uint8_t> got(len + 64);
+            const size_t k = fread(got.data(), 1, got.size(), in);
+            fclose(in);
+            const size_t pre = !strcmp(mode, "ab") ? 3 : 0;
+            if (k != pre + 4 + len + 4 || memcmp(got.data() + pre, "HEAD", 4) ||
+                memcmp(got.data() + pre + 4, arena.data(), len) || memcmp(got.data() + pre + 4 + len, "TAIL", 4))
+                return fail(mode);
+        }
+        remove(path.c_str());
         S.join();
         fclose(out);
     } else {

@@ -205,3 +205,72 @@ def test_loops_oracle_elementwise_and_untouched(oracle_bin, tmp_path):
          tmp_path / "y.bin", tmp_path / "z.bin", tmp_path / "zo.bin", "9"])
     got = np.fromfile(tmp_path / "zo.bin")
     assert got.tolist() == [1.0, 3.0, 5.0, -1.0, -1.0, -1.5, -2.0, -2.5, -3.0]
+
+
+# ------------------------------------------------------------------ synth
+
+def _f32(v):
+    return float(np.float32(v))
+
+
+def test_synth_oracle_hand_cases(oracle_bin, tmp_path):
+    """flops=1, no divergent branch: z = fmaf(sum of (float)x_k, 1.0001f, 0.5f);
+    with every iteration divergent, one more fmaf(., 0.9999f, -0.25f).  The
+    fused multiply-add rounds once, so values are checked through float64
+    arithmetic rounded once to float32 (exact for these operands)."""
+    trip, nw = 5, 3
+    x = np.array([0.5, 1.25, -2.0, 3.0, 0.0, 1.0, 2.0, 4.0, 8.0, 16.0, 0.25, 0.25, 0.25, 0.25, 0.25])
+    inputs.write_f64(tmp_path / "x.bin", x)
+
+    def go(div):
+        out = run([oracle_bin("synth"), str(trip), str(8 * nw), "1", str(div), "0", "9", tmp_path / "x.bin",
+                   tmp_path / "z.bin"])
+        return out, np.fromfile(tmp_path / "z.bin")
+
+    out, z = go(0)
+    assert out.strip() == "rpc 0"
+    for i in range(trip):
+        acc = _f32(_f32(_f32(0.0 + _f32(x[i])) + _f32(x[trip + i])) + _f32(x[2 * trip + i]))
+        assert z[i] == _f32(acc * _f32(1.0001) + 0.5)
+    out, z2 = go(2 ** 32 - 1)
+    for i in range(trip):
+        assert z2[i] == _f32(z[i] * _f32(0.9999) - 0.25)
+
+
+def test_synth_oracle_rpc_count(oracle_bin, tmp_path):
+    trip = 4096
+    inputs.write_f64(tmp_path / "x.bin", np.zeros(trip))
+    thresh = 2 ** 28                                   # 1/16 of the iterations
+    out = run([oracle_bin("synth"), str(trip), "8", "1", "0", str(thresh), "3", tmp_path / "x.bin",
+               tmp_path / "z.bin"])
+    want = sum(1 for i in range(trip) if (_mix((3 + i * 0x9E3779B97F4A7C15) & MASK) >> 32) < thresh)
+    assert out.strip() == f"rpc {want}"
+
+
+# ------------------------------------------------------------------ spmv_serve
+
+def test_spmv_serve_oracle_hand_case(oracle_bin, tmp_path, monkeypatch):
+    """A 3x3 matrix, two passes, one request of each kind checked by hand."""
+    monkeypatch.setenv("GF_SERVE_VAR1", "abc")
+    monkeypatch.delenv("GF_SERVE_VAR2", raising=False)
+    rowptr = np.array([0, 2, 3, 4], dtype=np.int64)
+    col = np.array([0, 2, 1, 0], dtype=np.int32)
+    val = np.array([2.0, 1.0, 3.0, -1.0])
+    x = np.array([1.0, 2.0, 4.0])
+    # pass 0: row 0 fwrite 5 bytes, row 1 printf, row 2 getenv (row % 3 = 2: unset); pass 1: row 1 getenv, row 2 clock
+    req = np.array([(0 << 32) | 0, 0 | (5 << 8), (0 << 32) | 1, 1, (0 << 32) | 2, 3,
+                    (1 << 32) | 1, 3, (1 << 32) | 2, 2], dtype=np.int64)
+    for name, a in [("rp", rowptr), ("c", col), ("v", val), ("x", x), ("q", req)]:
+        inputs.write_raw(tmp_path / f"{name}.bin", a)
+    out = run([oracle_bin("spmv_serve"), "7", "2", "3", "4", "5", tmp_path / "rp.bin", tmp_path / "c.bin",
+               tmp_path / "v.bin", tmp_path / "x.bin", tmp_path / "q.bin", tmp_path / "y.bin",
+               tmp_path / "rec.bin", tmp_path / "res.bin"])
+    # pass 0: y = [2*1 + 1*4, 3*2, -1*1] = [6, 6, -1]; pass 1: y = [2*6 + 1*(-1), 3*6, -1*6] = [11, 18, -6]
+    assert np.fromfile(tmp_path / "y.bin").tolist() == [11.0, 18.0, -6.0]
+    assert out == "p 7 r 0 row 1 y 6\n"
+    rec = (tmp_path / "rec.bin").read_bytes()
+    assert rec[:16] == np.array([7, 0, 0, 5], dtype=np.uint32).tobytes()
+    key = _mix((7 << 40) ^ (0 << 32) ^ 0)
+    assert rec[16:] == (_mix(key) & MASK).to_bytes(8, "little")[:5]
+    res = np.fromfile(tmp_path / "res.bin", dtype=np.int64)
+    assert res[0] == 21 and res[1] == len(out) and res[2] == -1 and res[3] == 3
