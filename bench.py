@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 N, SWEEPS = 256, 100
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_PER_POINT = 9
+FP64_OPS_PER_POINT = 7
 # DRAM bytes (read + write) of one full launch, scaled from an ncu capture of
 # 20 sweeps without the final write (profiles/jacobi_256_sweeps_ncu.md):
 # per sweep x 100 + the 128 MiB read of the final fwrite.  None until captured
@@ -66,6 +66,28 @@ def hbm_peak():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def default_out_dir():
+    """/dev/shm when it is a writable directory, else the system temp dir."""
+    d = "/dev/shm"
+    return d if os.path.isdir(d) and os.access(d, os.W_OK) else None
+
+
+def fs_type(path):
+    """File system type of the mount holding path (from /proc/mounts), or None."""
+    try:
+        best, kind = "", None
+        real = os.path.realpath(path)
+        with open("/proc/mounts") as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 3 and (real == parts[1] or real.startswith(parts[1].rstrip("/") + "/")) \
+                        and len(parts[1]) > len(best):
+                    best, kind = parts[1], parts[2]
+        return kind
+    except OSError:
+        return None
 
 
 class Clocks:
@@ -129,7 +151,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    tmp = tempfile.mkdtemp(prefix="gfbench")
+    tmp = tempfile.mkdtemp(prefix="gfbench", dir=args.out_dir or default_out_dir())
     sample = max(1, args.ref_sweeps)
     for _ in range(args.warmup):
         cpu_oracle_sample(N, sample, tmp)
@@ -160,8 +182,13 @@ def main():
     ap.add_argument("--impl", default="gf", choices=["gf", "reference"])
     ap.add_argument("--ref-sweeps", type=int, default=4)
     ap.add_argument("--cpu-sweeps", type=int, default=8)
-    ap.add_argument("--out-dir", default=None, help="where the program writes its final grid")
+    ap.add_argument("--out-dir", default=None,
+                    help="where the program writes its final grid (default: /dev/shm when it is a writable "
+                         "tmpfs, so the number measures the runtime and the page cache, not the disk)")
     ap.add_argument("--sweeps", type=int, default=SWEEPS, help="sweeps per program (100 = the benchmark workload)")
+    ap.add_argument("--int-adds", type=int, default=None,
+                    help="how many of the five neighbour adds run on the integer pipe (0..5; the program's "
+                         "default when omitted)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--no-write", action="store_true",
                     help="the program skips its final fwrite (profiling runs that isolate the sweeps)")
@@ -188,7 +215,8 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    tmp = tempfile.mkdtemp(prefix="gfbench", dir=args.out_dir)
+    out_dir = args.out_dir or default_out_dir()
+    tmp = tempfile.mkdtemp(prefix="gfbench", dir=out_dir)
     out_path = os.path.join(tmp, f"grid_r{rank}.bin")
 
     g = inputs.jacobi_input(N, seed=2)
@@ -199,6 +227,8 @@ def main():
     ctx = gf.Context(stream=stream, heap_bytes=heap, heap_small_pct=5,
                      stdout_path=os.path.join(tmp, f"stdout_r{rank}.txt"))
     argv = [N, sweeps, "-" if args.no_write else out_path]
+    if args.int_adds is not None:
+        argv.append(args.int_adds)
 
     def step(buf):
         rc, ec = ctx.run("jacobi", argv, [(buf, gf.GF_BUF_IN)])
@@ -245,22 +275,23 @@ def main():
         e2e = loop_bytes(N, sweeps) * e2e_steps * world / e2e_t / 1e9
 
     peak, peak_kind = hbm_peak()
-    achieved = loop_bytes(N, sweeps) / (total / args.steps) / 1e9
-    # The sweep is bound by GB300's FP64 pipe, not HBM: 9 FP64 instructions per
-    # interior point at minimum for results bit-equal to the serial program
-    # (5 + 1 adds, and the correctly rounded /6 as 1 DMUL + 2 DFMA), and the
-    # pipe retires 2 thread-instructions per clock per SM (ncu: 16 cycles of
-    # sm__pipe_fp64_cycles_active per warp instruction).
+    # Algorithmic bytes of one launch: every sweep reads the grid once and
+    # writes the new one (2 x 8 B per point), and the final fwrite reads the
+    # last grid once more.
+    launch_bytes = loop_bytes(N, sweeps) + (0 if args.no_write else 8 * N ** 3)
+    achieved = launch_bytes / (total / args.steps) / 1e9
+    sweep_s = max(st.region_ns, 1) / max(1, st.regions) / 1e9
+    # GB300 retires 2 FP64 lanes per clock per SM; a sweep's 7 FP64 operations
+    # per interior point (5 adds, the /6, the residual's subtract) all on that
+    # pipe would take this long.  The program moves part of them to the
+    # integer pipe (bit-identical results) to get below it.
     sms = ctx.grid_info("jacobi")[0]
     sm_mhz = 2070.0
     try:
         sm_mhz = float(json.load(open(PEAKS)).get("sm_max_mhz", sm_mhz))
     except Exception:
         pass
-    fp64_peak = sms * 2 * sm_mhz * 1e6 / 1e9                        # G FP64 instructions / s
-    fp64_per_launch = FP64_PER_POINT * (N - 2) ** 3 * sweeps
-    alu_achieved = fp64_per_launch / (total / args.steps) / 1e9
-    alu_sweeps = fp64_per_launch / (st.region_ns / 1e9) / 1e9 if st.region_ns else None
+    fp64_only_sweep_s = FP64_OPS_PER_POINT * (N - 2) ** 3 / (sms * 2 * sm_mhz * 1e6)
     cpu = None
     if rank == 0 and args.cpu_sweeps > 0:
         cv, cdt = cpu_oracle_sample(N, args.cpu_sweeps, tmp)
@@ -275,16 +306,17 @@ def main():
             "config": {"workload": f"jacobi-7pt {N}^3 fp64, {sweeps} sweeps, per-sweep device malloc/free, "
                                    "fused max-residual, printf per sweep, final fwrite",
                        "grid": st.grid, "block": st.block, "l2": "inputs larger than L2 (2 x 134 MB grids)",
+                       "output": None if args.no_write else {"dir": os.path.dirname(tmp), "fs": fs_type(tmp)},
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "alu", "achieved": round(alu_achieved, 1), "peak": round(fp64_peak, 1),
-                         "unit": "G FP64 instr/s", "frac": round(alu_achieved / fp64_peak, 4),
-                         "traffic": TRAFFIC_PER_LAUNCH,
-                         "peak_kind": "derived: SMs x 2 FP64 lanes/clk x max SM clock",
-                         "kernel": "program_kernel<jacobi>",
-                         "sweeps_only": None if alu_sweeps is None else
-                         {"achieved": round(alu_sweeps, 1), "frac": round(alu_sweeps / fp64_peak, 4)},
-                         "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind}},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": TRAFFIC_PER_LAUNCH,
+                         "peak_kind": peak_kind, "kernel": "program_kernel<jacobi>",
+                         "algorithmic_bytes_per_launch": launch_bytes,
+                         "sweeps_only": {"achieved": round(loop_bytes(N, 1) / sweep_s / 1e9, 1),
+                                         "frac": round(loop_bytes(N, 1) / sweep_s / 1e9 / peak, 4),
+                                         "sweep_us": round(sweep_s * 1e6, 2)},
+                         "fp64_pipe": {"fp64_only_sweep_us": round(fp64_only_sweep_s * 1e6, 1),
+                                       "sweep_vs_fp64_only": round(sweep_s / fp64_only_sweep_s, 3)}},
             "e2e": None if e2e is None else {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": N ** 3 * 8,
                     "d2h_bytes_per_step": N ** 3 * 8 + 100 * 24},
             "gpu_launches": args.steps,

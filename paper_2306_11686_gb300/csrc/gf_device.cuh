@@ -332,6 +332,9 @@ template <class F> __device__ __forceinline__ void run_schedule(const gf_region 
     const int64_t b = rd->b, e = rd->e, c = rd->chunk;
     if (rd->sched == GF_SCHED_STATIC) {
         if (c == 1) {
+            /* two iterations in flight per thread: their dependent chains of
+             * long-latency operations (FP64, loads) overlap */
+#pragma unroll 2
             for (int64_t i = b + w.tid; i < e; i += w.nthreads)
                 f(i);
         } else if (c <= 0) {                       /* OpenMP default: one contiguous block each */

@@ -11,12 +11,17 @@
  *  - the small region is cut into 256 KiB slabs; a slab belongs to one class and
  *    to the SM that first took it (slab metadata gives any block's size, which
  *    is the allocation tracking the paper needs for pointer lookup, Sec. 3.2);
- *  - each (SM, class) pair has a lock-free LIFO of freed blocks (Treiber stack
- *    with a 32-bit ABA tag in the 64-bit head) and a current slab served by an
- *    atomic bump counter;
- *  - a warp's lanes that ask for the same class are served by one leader
- *    (__match_any_sync): one CAS pops up to 32 blocks, one atomicAdd bumps up
- *    to 32; frees are chained per (owner SM, class) and pushed with one CAS;
+ *  - each (SM, class) pair has 32 lock-free LIFOs of freed blocks, one per
+ *    lane index (Treiber stacks with a 32-bit ABA tag in the 64-bit head), and
+ *    a current slab served by an atomic bump counter;
+ *  - every lane pops and pushes its own block on the stack of its lane index,
+ *    so a warp's 32 requests are 32 independent CASes issued together: no
+ *    list is walked (a single stack per (SM, class) would need a warp's leader
+ *    to follow 32 dependent next-links, about 16 us, before its one CAS);
+ *  - lanes whose stack is empty are served together by one bump of the
+ *    current slab (the leader of the lanes that ask for the same class,
+ *    __match_any_sync); with no fresh slab left they take blocks from the
+ *    other stacks of their SM, then of the other SMs, before failing;
  *  - sizes above 64 KiB take 64 KiB pages first-fit from a sorted extent list
  *    under one device lock (rare; the paper notes large serial-part
  *    allocations come from the initial thread, Sec. 3.4).
@@ -50,42 +55,61 @@ __device__ __forceinline__ uint32_t *curs(gf_heap *H) { return (uint32_t *)H->cu
 __device__ __forceinline__ uint64_t node_addr(gf_heap *H, uint32_t node1) { return H->slab_base + ((uint64_t)(node1 - 1) << 4); }
 __device__ __forceinline__ uint32_t node_of(gf_heap *H, uint64_t addr) { return (uint32_t)((addr - H->slab_base) >> 4) + 1; }
 
-/* pop up to k blocks of (sm, cls); writes addresses to out[member lanes in mask order] */
-static __device__ uint32_t heap_pop(gf_heap *H, uint32_t sm, uint32_t cls, uint32_t k, uint64_t *out, uint32_t mask)
+__device__ __forceinline__ unsigned long long *stack_of(gf_heap *H, uint32_t sm, uint32_t cls, uint32_t sub)
 {
-    unsigned long long *head = &heads(H)[sm * GF_HEAP_NCLASS + cls];
+    return &heads(H)[((size_t)sm * GF_HEAP_NCLASS + cls) * GF_HEAP_LANES + sub];
+}
+
+/* pop one block from stack (sm, cls, sub); 0 if it is empty (or stays contended) */
+static __device__ __forceinline__ uint64_t heap_pop1(gf_heap *H, uint32_t sm, uint32_t cls, uint32_t sub)
+{
+    unsigned long long *head = stack_of(H, sm, cls, sub);
     const uint32_t max1 = (uint32_t)(H->slab_bytes >> 4);
     for (int attempt = 0; attempt < 64; attempt++) {
         const unsigned long long h = *(volatile unsigned long long *)head;
-        uint32_t cur = (uint32_t)h;
+        const uint32_t cur = (uint32_t)h;
         if (cur == 0)
             return 0;
-        uint32_t cnt = 0;
-        uint32_t m = mask;
-        bool ok = true;
-        uint32_t after = 0;
-        for (;;) {
-            const uint32_t l = __ffs(m) - 1;
-            m &= m - 1;
-            out[l] = node_addr(H, cur);
-            cnt++;
-            const uint32_t nxt = *(volatile uint32_t *)node_addr(H, cur);
-            if (nxt > max1) {          /* block reused under us: the CAS below must fail */
-                ok = false;
-                break;
-            }
-            if (cnt == k || nxt == 0) {
-                after = nxt;
-                break;
-            }
-            cur = nxt;
-        }
-        if (!ok)
+        const uint32_t nxt = *(volatile uint32_t *)node_addr(H, cur);
+        if (nxt > max1)                /* block reused under us: the CAS would fail */
             continue;
-        const unsigned long long nh = ((h >> 32) + 1ull) << 32 | after;
-        if (atomicCAS(head, h, nh) == h) {
+        if (atomicCAS(head, h, ((h >> 32) + 1ull) << 32 | nxt) == h) {
             __threadfence();
-            return cnt;
+            return node_addr(H, cur);
+        }
+    }
+    return 0;
+}
+
+/* push block a (node index node) onto stack (sm, cls, sub); false after a
+ * contention bound no sane run reaches */
+static __device__ __forceinline__ bool heap_push1(gf_heap *H, uint32_t sm, uint32_t cls, uint32_t sub, uint64_t a,
+                                                   uint32_t node)
+{
+    unsigned long long *head = stack_of(H, sm, cls, sub);
+    for (int attempt = 0; attempt < (1 << 20); attempt++) {
+        const unsigned long long h = *(volatile unsigned long long *)head;
+        *(volatile uint32_t *)a = (uint32_t)h;
+        __threadfence();
+        if (atomicCAS(head, h, ((h >> 32) + 1ull) << 32 | node) == h)
+            return true;
+    }
+    return false;
+}
+
+/* a block of (cls) from any stack other than (sm, cls, own): the rest of this
+ * SM's stacks first, then the other SMs' */
+static __device__ uint64_t heap_steal1(gf_heap *H, uint32_t sm, uint32_t cls, uint32_t own)
+{
+    for (uint32_t o = 0; o < GF_MAX_SM; o++) {
+        const uint32_t s = (sm + o) % GF_MAX_SM;
+        for (uint32_t j = o ? 0 : 1; j < GF_HEAP_LANES; j++) {
+            const uint32_t sub = (own + j) % GF_HEAP_LANES;
+            if ((uint32_t)*(volatile unsigned long long *)stack_of(H, s, cls, sub) == 0)
+                continue;
+            const uint64_t p = heap_pop1(H, s, cls, sub);
+            if (p)
+                return p;
         }
     }
     return 0;
@@ -268,41 +292,40 @@ static __device__ __noinline__ void *gf_malloc(size_t n)
     const uint32_t active = __activemask();
     const uint32_t grp = __match_any_sync(active, cls);
     const uint32_t leader = __ffs(grp) - 1;
+    const uint32_t sm = gfd::smid() % GF_MAX_SM;
     uint64_t *out = gfd::s_xfer[warp];
-    if (lane == leader) {
-        const uint32_t k = __popc(grp);
-        const uint32_t sm = gfd::smid() % GF_MAX_SM;
-        uint32_t got = gfd::heap_pop(H, sm, cls, k, out, grp);
-        uint32_t rest = grp;
-        for (uint32_t j = 0; j < got; j++)
-            rest &= rest - 1;
-        if (got < k)
-            got += gfd::heap_bump(H, sm, cls, k - got, out, rest);
-        if (got < k) {                 /* drain other SMs' free stacks before failing */
-            for (uint32_t o = 1; o < GF_MAX_SM && got < k; o++) {
-                uint32_t r2 = grp;
-                for (uint32_t j = 0; j < got; j++)
-                    r2 &= r2 - 1;
-                got += gfd::heap_pop(H, (sm + o) % GF_MAX_SM, cls, k - got, out, r2);
-            }
+    /* every lane: its own stack */
+    uint64_t p = gfd::heap_pop1(H, sm, cls, lane);
+    /* the lanes left empty-handed: one bump of the current slab for the group */
+    const uint32_t miss = __ballot_sync(grp, p == 0) & grp;
+    if (miss) {
+        if (lane == leader) {
+            const uint32_t got = gfd::heap_bump(H, sm, cls, __popc(miss), out, miss);
+            uint32_t r = miss;
+            for (uint32_t j = 0; j < got; j++)
+                r &= r - 1;
+            for (; r; r &= r - 1)
+                out[__ffs(r) - 1] = 0;
+            __threadfence_block();
         }
-        uint32_t r3 = grp;
-        for (uint32_t j = 0; j < got; j++)
-            r3 &= r3 - 1;
-        for (; r3; r3 &= r3 - 1)
-            out[__ffs(r3) - 1] = 0;
+        __syncwarp(grp);
+        if (!p)
+            p = out[lane];
+        __syncwarp(grp);
+        if (!p)                        /* no fresh slab: other stacks before failing */
+            p = gfd::heap_steal1(H, sm, cls, lane);
+    }
+    const uint32_t ok = __ballot_sync(grp, p != 0) & grp;
+    if (lane == leader) {
+        const uint32_t got = __popc(ok), k = __popc(grp);
         const unsigned long long bs = 16ull << cls;
         atomicAdd((unsigned long long *)&H->n_alloc, (unsigned long long)got);
         if (got < k)
             atomicAdd((unsigned long long *)&H->n_fail, (unsigned long long)(k - got));
         const unsigned long long live = atomicAdd((unsigned long long *)&H->live_bytes, bs * got) + bs * got;
         atomicMax((unsigned long long *)&H->high_water, live);
-        __threadfence_block();
     }
-    __syncwarp(grp);
-    void *p = (void *)gfd::s_xfer[warp][lane];
-    __syncwarp(grp);
-    return p;
+    return (void *)p;
 }
 
 static __device__ __noinline__ void gf_free(void *p)
@@ -341,38 +364,17 @@ static __device__ __noinline__ void gf_free(void *p)
         atomicAdd((unsigned long long *)&H->n_bad_free, 1ull);
         return;
     }
-    /* chain this group's blocks in lane order and push the chain with one CAS */
-    const uint32_t node = gfd::node_of(H, a);
-    const uint32_t higher = grp & ~((2u << lane) - 1u);
-    const uint32_t next_lane = higher ? __ffs(higher) - 1 : lane;
-    const uint32_t next_node = __shfl_sync(grp, node, next_lane);
-    const uint32_t last_lane = 31 - __clz(grp);
-    const uint32_t leader = __ffs(grp) - 1;
-    const uint32_t first_node = __shfl_sync(grp, node, leader);
-    if (higher)
-        *(volatile uint32_t *)p = next_node;
-    const uint32_t last_node = __shfl_sync(grp, node, last_lane);
-    __threadfence();
-    __syncwarp(grp);
-    if (lane == leader) {
-        const uint32_t n = __popc(grp);
+    /* every lane pushes its block on the stack of its lane index */
+    const bool pushed = gfd::heap_push1(H, owner, cls, lane, a, gfd::node_of(H, a));
+    if (!pushed)                       /* contention beyond reason: the block leaks */
+        gfd::set_error(GF_ETIMEDOUT);
+    const uint32_t done = __ballot_sync(grp, pushed) & grp;
+    if (lane == __ffs(grp) - 1) {
         const unsigned long long bs = 16ull << cls;
-        atomicAdd((unsigned long long *)&H->n_free, (unsigned long long)n);
-        atomicAdd((unsigned long long *)&H->live_bytes, (unsigned long long)(0ull - bs * n));
-        unsigned long long *head = &gfd::heads(H)[owner * GF_HEAP_NCLASS + cls];
-        volatile uint32_t *lastp = (volatile uint32_t *)gfd::node_addr(H, last_node);
-        bool pushed = false;
-        for (int attempt = 0; attempt < (1 << 20) && !pushed; attempt++) {
-            const unsigned long long h = *(volatile unsigned long long *)head;
-            *lastp = (uint32_t)h;
-            __threadfence();
-            const unsigned long long nh = ((h >> 32) + 1ull) << 32 | first_node;
-            pushed = atomicCAS(head, h, nh) == h;
-        }
-        if (!pushed)                          /* contention beyond reason: the blocks leak */
-            gfd::set_error(GF_ETIMEDOUT);
+        const unsigned long long nd = (unsigned long long)__popc(done);
+        atomicAdd((unsigned long long *)&H->n_free, nd);
+        atomicAdd((unsigned long long *)&H->live_bytes, 0ull - bs * nd);
     }
-    __syncwarp(grp);
 }
 
 /* size of the heap block holding p (0 if p is not a live heap block start) */

@@ -28,6 +28,7 @@
 #define GF_DEVICE_LIBC_CUH
 
 #include "gf_device.cuh"
+#include "gf_strtod_fast.h"
 
 #define GF_OP_STRTOD_LIT GF_OP_STRTOD   /* the host strtod landing pad */
 
@@ -139,68 +140,12 @@ __device__ inline void *gf_realloc(void *p, size_t n)
 
 __device__ inline double gf_strtod(const char *str, char **endptr)
 {
-    const char *p = str;
-    while (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r' || *p == '\f' || *p == '\v')
-        p++;
-    bool neg = false;
-    if (*p == '+' || *p == '-')
-        neg = (*p++ == '-');
-    unsigned long long mant = 0;
-    int digits = 0, exp10 = 0;
-    bool any = false, fast = true;
-    for (; *p >= '0' && *p <= '9'; p++) {
-        any = true;
-        if (mant == 0 && *p == '0')
-            continue;                          /* leading zeros are not significant */
-        if (digits < 19) {
-            mant = mant * 10 + (unsigned)(*p - '0');
-            digits++;
-        } else {
-            fast = false;
-        }
-    }
-    if (*p == '.') {
-        p++;
-        for (; *p >= '0' && *p <= '9'; p++) {
-            any = true;
-            if (mant == 0 && *p == '0') {
-                exp10--;
-                continue;
-            }
-            if (digits < 19) {
-                mant = mant * 10 + (unsigned)(*p - '0');
-                digits++;
-                exp10--;
-            } else {
-                fast = false;
-            }
-        }
-    }
-    if (!any)
-        fast = false;                          /* inf, nan, hex, or no number: let the host decide */
-    if (any && (*p == 'e' || *p == 'E')) {
-        const char *q = p + 1;
-        bool eneg = false;
-        if (*q == '+' || *q == '-')
-            eneg = (*q++ == '-');
-        if (*q >= '0' && *q <= '9') {
-            int e = 0;
-            for (; *q >= '0' && *q <= '9'; q++)
-                e = e < 100000 ? e * 10 + (*q - '0') : e;
-            exp10 += eneg ? -e : e;
-            p = q;
-        }
-    }
-    if (fast && digits <= 15 && exp10 >= -22 && exp10 <= 22) {
-        const int ae = exp10 < 0 ? -exp10 : exp10;
-        double p10 = 1.0;                      /* 10^k for k <= 22 is exact, and so is each step */
-        for (int k = 0; k < ae; k++)
-            p10 = __dmul_rn(p10, 10.0);
-        double v = (double)mant;               /* exact: mant < 10^15 < 2^53 */
-        v = exp10 >= 0 ? __dmul_rn(v, p10) : __ddiv_rn(v, p10);
+    double v;
+    const char *end;
+    if (gf_strtod_fast(str, &v, &end)) {
         if (endptr)
-            *endptr = (char *)p;
-        return neg ? -v : v;
+            *endptr = (char *)end;
+        return v;
     }
     /* exact slow path on the host: value bits returned, consumed length written back */
     long long used = 0;

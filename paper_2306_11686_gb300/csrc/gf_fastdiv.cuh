@@ -1,5 +1,6 @@
 /*
- * Correctly rounded division by the constant 6.0 in three FP64 operations.
+ * Correctly rounded division by the constant 6.0 in three FP64 operations
+ * (the integer-pipe version, gf_div6_int, is in gf_intpipe.cuh).
  *
  * GB300 issues FP64 instructions at a small fraction of its other rates, and
  * a general IEEE double division costs several of them; a compiler may

@@ -118,6 +118,7 @@ typedef struct gf_region {
 #define GF_SLAB_SHIFT 18        /* 256 KiB slabs                                      */
 #define GF_PAGE_SHIFT 16        /* 64 KiB pages for the large path                    */
 #define GF_MAX_SM 256
+#define GF_HEAP_LANES 32        /* free stacks per (SM, class): one per lane index    */
 #define GF_LARGE_EXT_MAX 8192   /* free extents of the large path                     */
 
 typedef struct gf_heap {
@@ -128,7 +129,7 @@ typedef struct gf_heap {
     uint64_t large_base;       /* [large_base, large_base + large_bytes): pages       */
     uint64_t large_bytes;
     uint64_t slab_meta;        /* device: per-slab {class, owner sm, bump} words      */
-    uint64_t free_heads;       /* device: [GF_MAX_SM][NCLASS] tagged stack heads      */
+    uint64_t free_heads;       /* device: [GF_MAX_SM][NCLASS][LANES] tagged heads     */
     uint64_t cur_slab;         /* device: [GF_MAX_SM][NCLASS] current slab + 1        */
     uint64_t large_ext;        /* device: free extents {page, npages} sorted          */
     uint64_t large_size;       /* device: npages of the block starting at each page   */

@@ -1,5 +1,6 @@
 /* Host RPC server: slot scanning and the libc landing pads (see server.h). */
 #include "server.h"
+#include "fmt_fast.h"
 
 #include <fcntl.h>
 #include <stdlib.h>
@@ -94,7 +95,8 @@ static size_t big_fwrite(const void *src, size_t size, size_t nmemb, FILE *f)
         return bad ? 0 : fwrite(src, size, nmemb, f);
     }
     unsigned char *dst = (unsigned char *)m + (pos - mstart);
-    const unsigned nthr = 8;
+    const unsigned hw = std::thread::hardware_concurrency();
+    const unsigned nthr = hw < 4 ? 4 : hw > 16 ? 16 : hw;   /* page faults of distinct pages run in parallel */
     const uint64_t part = ((n + nthr - 1) / nthr + 4095) & ~4095ull;
     std::vector<std::thread> th;
     for (unsigned t = 0; t < nthr; t++) {
@@ -189,6 +191,8 @@ void Server::emit(uint64_t stream, const std::string &s)
  * with exactly that conversion and an argument of the C type it names.  The
  * output equals one printf call with the same arguments, because printf's
  * output is the concatenation of its literal text and its conversions.
+ * Plain conversions (no flags, width or '*') go through gfh::fmt_fast
+ * (std::to_chars, the same characters) instead of snprintf.
  */
 int64_t Server::do_printf(const char *fmt, const uint8_t *recp, std::string &out, uint64_t *stream)
 {
@@ -216,21 +220,29 @@ int64_t Server::do_printf(const char *fmt, const uint8_t *recp, std::string &out
         const char *s0 = p++;
         while (*p && strchr("-+ #0'", *p))
             p++;
-        int star_w = 0, star_p = 0;
+        const bool flags = p != s0 + 1;
+        bool width = false;
+        int star_w = 0, star_p = 0, prec = -1;
         if (*p == '*') {
             star_w = 1;
             p++;
         } else
-            while (*p >= '0' && *p <= '9')
+            while (*p >= '0' && *p <= '9') {
+                width = true;
                 p++;
+            }
         if (*p == '.') {
             p++;
             if (*p == '*') {
                 star_p = 1;
                 p++;
-            } else
-                while (*p >= '0' && *p <= '9')
+            } else {
+                prec = 0;
+                while (*p >= '0' && *p <= '9') {
+                    prec = prec < 100000 ? prec * 10 + (*p - '0') : prec;
                     p++;
+                }
+            }
         }
         char len[3] = {0, 0, 0};
         if (*p == 'h' || *p == 'l') {
@@ -270,6 +282,11 @@ int64_t Server::do_printf(const char *fmt, const uint8_t *recp, std::string &out
         const uint32_t k = ai++;
         const uint64_t w = r.word(k);
         int n = 0;
+        if (!flags && !width && !star_w && !star_p &&
+            gfh::fmt_fast(conv, len, prec, w, r.tag(k) == GF_T_F64, buf, sizeof(buf), &n)) {
+            out.append(buf, (size_t)n);
+            continue;
+        }
         char *dst = buf;
         std::string big;
 #define GF_FMT(VAL)                                                                                 \

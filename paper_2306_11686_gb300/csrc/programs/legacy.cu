@@ -8,6 +8,7 @@
  */
 #include "../gf_device.cuh"
 #include "../gf_fastdiv.cuh"
+#include "../gf_intpipe.cuh"
 
 /*
  * axpy_sum N out_path            buffers: 0 = x (N doubles), 1 = y (N doubles, updated)
@@ -49,24 +50,68 @@ GF_MAIN(axpy_sum)(int argc, char **argv)
 }
 
 /*
- * jacobi n sweeps out_path       buffers: 0 = input grid (n^3 doubles, i fastest)
+ * One Jacobi sweep: the six-neighbour average of the interior into un, 0 on
+ * the boundary, and the max residual |un - u| over the grid as a max
+ * reduction.  The five neighbour adds keep the serial program's order; the
+ * first INT_ADDS of them run on the integer pipe and the rest on the FP64
+ * pipe (every one correctly rounded, so the split changes no bit of the
+ * result, only which pipe does the work), as do the division by 6 and the
+ * absolute value.  The flat index is split into (i, j, k) by multiplication
+ * with an invariant-divisor magic number.
+ */
+template <int INT_ADDS>
+__device__ int jacobi_sweep(const double *u, double *un, uint32_t nn, uint64_t cells, double *res)
+{
+    const uint32_t sk = nn * nn;
+    const gf_udiv32 dn = gf_udiv32::make(nn);
+    return gf_reduce<double, GF_RED_MAX>(
+        0, (int64_t)cells, GF_SCHED_STATIC, 1,
+        [=](int64_t c64) -> double {
+            const uint32_t c = (uint32_t)c64;
+            const uint32_t jk = dn.div(c), i = c - jk * nn;
+            const uint32_t k = dn.div(jk), j = jk - k * nn;
+            if (i == 0 || j == 0 || k == 0 || i == nn - 1 || j == nn - 1 || k == nn - 1) {
+                un[c] = 0.0;
+                return 0.0;
+            }
+            /* u is not written during the sweep: read-only loads, which may be
+             * issued ahead of the previous iteration's store to un */
+            const double nb[6] = {__ldg(u + c - 1),  __ldg(u + c + 1),  __ldg(u + c - nn),
+                                  __ldg(u + c + nn), __ldg(u + c - sk), __ldg(u + c + sk)};
+            double v = nb[0];
+#pragma unroll
+            for (int t = 1; t < 6; t++)
+                v = t <= INT_ADDS ? gf_dadd_int(v, nb[t]) : __dadd_rn(v, nb[t]);
+            v = gf_div6_int(v);               /* == v / 6.0, bit for bit */
+            un[c] = v;
+            return gf_fabs_int(__dadd_rn(v, -__ldg(u + c)));
+        },
+        res);
+}
+
+/*
+ * jacobi n sweeps out_path [int_adds]   buffers: 0 = input grid (n^3 doubles, i fastest)
  *
  * Laplace Jacobi sweeps with the six-neighbour average, boundary written as 0,
  * a fresh grid from the device heap every sweep (old one freed after the
  * swap), the max residual over the interior fused into the sweep as a max
- * reduction, one printf per sweep, the final grid fwrite'd.
+ * reduction, one printf per sweep, the final grid fwrite'd.  int_adds (0..5,
+ * default 1) is how many of the five neighbour adds run on the integer pipe.
+ * Compiled for 4 resident blocks per SM (64 registers): the sweep waits on
+ * L2 more than on any pipe, and more warps hide that latency.
  */
-GF_MAIN(jacobi)(int argc, char **argv)
+GF_MAIN_BOUNDS(jacobi, 4)(int argc, char **argv)
 {
     if (argc < 4)
         return 2;
     const long long n = gf_atoll(argv[1]);
     const int sweeps = (int)gf_atoll(argv[2]);
+    const int int_adds = argc > 4 ? (int)gf_atoll(argv[4]) : 1;
     const double *u0 = (const double *)gf_buffer(0);
     const uint64_t cells = (uint64_t)n * n * n;
-    if (n < 1 || n > 1290 || !u0 || gf_buffer_bytes(0) < cells * 8)
+    if (n < 1 || n > 1290 || !u0 || gf_buffer_bytes(0) < cells * 8 || int_adds < 0 || int_adds > 5)
         return 2;
-    const uint32_t nn = (uint32_t)n, sk = nn * nn;
+    const uint32_t nn = (uint32_t)n;
     const double *u = u0;
     double *owned = nullptr;
     for (int s = 1; s <= sweeps; s++) {
@@ -76,25 +121,15 @@ GF_MAIN(jacobi)(int argc, char **argv)
             return 4;
         }
         double res = 0.0;
-        int rc = gf_reduce<double, GF_RED_MAX>(
-            0, (int64_t)cells, GF_SCHED_STATIC, 1,
-            [=](int64_t c64) -> double {
-                const uint32_t c = (uint32_t)c64;
-                const uint32_t i = c % nn, jk = c / nn, j = jk % nn, k = jk / nn;
-                if (i == 0 || j == 0 || k == 0 || i == nn - 1 || j == nn - 1 || k == nn - 1) {
-                    un[c] = 0.0;
-                    return 0.0;
-                }
-                double v = u[c - 1] + u[c + 1];
-                v = v + u[c - nn];
-                v = v + u[c + nn];
-                v = v + u[c - sk];
-                v = v + u[c + sk];
-                v = gf_div6_rn(v);            /* == v / 6.0, bit for bit */
-                un[c] = v;
-                return fabs(v - u[c]);
-            },
-            &res);
+        int rc;
+        switch (int_adds) {
+        case 0: rc = jacobi_sweep<0>(u, un, nn, cells, &res); break;
+        case 1: rc = jacobi_sweep<1>(u, un, nn, cells, &res); break;
+        case 2: rc = jacobi_sweep<2>(u, un, nn, cells, &res); break;
+        case 3: rc = jacobi_sweep<3>(u, un, nn, cells, &res); break;
+        case 4: rc = jacobi_sweep<4>(u, un, nn, cells, &res); break;
+        default: rc = jacobi_sweep<5>(u, un, nn, cells, &res); break;
+        }
         if (rc)
             return 10;
         gf_printf("%d %.17g\n", s, res);

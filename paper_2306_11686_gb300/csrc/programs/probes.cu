@@ -5,6 +5,7 @@
  */
 #include "../gf_device.cuh"
 #include "../gf_fastdiv.cuh"
+#include "../gf_intpipe.cuh"
 
 /* sched_probe b e sched chunk      buffers: 0 = int32 hits[e-b], 1 = int64 owner[e-b], 2 = int64 info[2]
  * Every iteration records which continuous thread id ran it. */
@@ -242,6 +243,43 @@ GF_MAIN(heap_big)(int argc, char **argv)
     return 0;
 }
 
+/* heap_exhaust T per bytes          buffers: 0 = uint64 ptrs[2 * T * per]
+ * Phase 1: T threads each allocate `per` blocks of `bytes` until the small
+ * heap is exhausted (NULLs from then on); all of them are freed; phase 2
+ * allocates the same way again, which can only be served from the freed
+ * blocks on the per-lane stacks of every SM (no fresh slab is left); then
+ * everything is freed again. */
+GF_MAIN(heap_exhaust)(int argc, char **argv)
+{
+    if (argc < 4)
+        return 2;
+    const long long T = gf_atoll(argv[1]), per = gf_atoll(argv[2]);
+    const size_t bytes = (size_t)gf_atoll(argv[3]);
+    unsigned long long *ptrs = (unsigned long long *)gf_buffer(0);
+    if (T < 1 || per < 1 || !ptrs || gf_buffer_bytes(0) < (uint64_t)(2 * T * per) * 8)
+        return 2;
+    for (int phase = 0; phase < 2; phase++) {
+        unsigned long long *out = ptrs + (size_t)phase * T * per;
+        if (gf_parallel_for(0, T, GF_SCHED_STATIC, 1, [=](int64_t t) {
+                for (long long j = 0; j < per; j++) {
+                    void *p = gf_malloc(bytes);
+                    if (p)
+                        *(volatile unsigned long long *)p = (unsigned long long)(t * per + j);
+                    out[t * per + j] = (unsigned long long)p;
+                }
+            }))
+            return 10;
+        if (gf_parallel_for(0, T * per, GF_SCHED_STATIC, 1, [=](int64_t i) {
+                void *p = (void *)out[i];
+                if (p && *(volatile unsigned long long *)p != (unsigned long long)i)
+                    out[i] |= 1ull;            /* a block shared by two owners: flag it */
+                gf_free(p);
+            }))
+            return 11;
+    }
+    return 0;
+}
+
 /* rpc_timeout                      the host does not serve: the call must come back with GF_ETIMEDOUT */
 GF_MAIN(rpc_timeout)(int argc, char **argv)
 {
@@ -250,7 +288,8 @@ GF_MAIN(rpc_timeout)(int argc, char **argv)
     return st == GF_ETIMEDOUT ? 1 : (st == GF_OK ? 0 : 2);
 }
 
-/* div6_probe n                     buffers: 0 = double x[n], 1 = double out[2n]: (x / 6.0, gf_div6_rn(x)) */
+/* div6_probe n                     buffers: 0 = double x[n],
+ *                                   1 = double out[3n]: (x / 6.0, gf_div6_rn(x), gf_div6_int(x)) */
 GF_MAIN(div6_probe)(int argc, char **argv)
 {
     const long long n = gf_atoll(argv[1]);
@@ -258,8 +297,23 @@ GF_MAIN(div6_probe)(int argc, char **argv)
     double *out = (double *)gf_buffer(1);
     return gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) {
         const double v = x[i];
-        out[2 * i] = v / 6.0;
-        out[2 * i + 1] = gf_div6_rn(v);
+        out[3 * i] = v / 6.0;
+        out[3 * i + 1] = gf_div6_rn(v);
+        out[3 * i + 2] = gf_div6_int(v);
+    }) ? 10 : 0;
+}
+
+/* dadd_probe n                     buffers: 0 = double x[n], 1 = double y[n],
+ *                                   2 = double out[2n]: (x + y on the FP64 pipe, gf_dadd_int(x, y)) */
+GF_MAIN(dadd_probe)(int argc, char **argv)
+{
+    const long long n = gf_atoll(argv[1]);
+    const double *x = (const double *)gf_buffer(0);
+    const double *y = (const double *)gf_buffer(1);
+    double *out = (double *)gf_buffer(2);
+    return gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) {
+        out[2 * i] = __dadd_rn(x[i], y[i]);
+        out[2 * i + 1] = gf_dadd_int(x[i], y[i]);
     }) ? 10 : 0;
 }
 

@@ -326,7 +326,7 @@ static int inst_alloc(gf_ctx *c, Instance *in)
     if (in->slab_bytes + in->large_bytes)
         GF_CK(cudaMalloc((void **)&in->d_heap, in->slab_bytes + in->large_bytes));
     GF_CK(cudaMalloc(&in->d_meta, (size_t)std::max<uint32_t>(in->nslabs, 1) * 16));
-    GF_CK(cudaMalloc(&in->d_heads, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 8));
+    GF_CK(cudaMalloc(&in->d_heads, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * GF_HEAP_LANES * 8));
     GF_CK(cudaMalloc(&in->d_cur, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 4));
     GF_CK(cudaMalloc(&in->d_ext, (size_t)GF_LARGE_EXT_MAX * 8));
     GF_CK(cudaMalloc(&in->d_lsize, (size_t)std::max<uint32_t>(in->npages, 1) * 4));
@@ -695,7 +695,7 @@ static int inst_start(gf_ctx *c, Instance *in, cudaStream_t stream, uint32_t gri
     in->h_ext0 = (uint64_t)0 | ((uint64_t)in->npages << 32);
     if (cudaMemcpyAsync(in->d_state, &s, sizeof s, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
         cudaMemsetAsync(in->d_meta, 0, (size_t)std::max<uint32_t>(in->nslabs, 1) * 16, stream) != cudaSuccess ||
-        cudaMemsetAsync(in->d_heads, 0, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 8, stream) != cudaSuccess ||
+        cudaMemsetAsync(in->d_heads, 0, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * GF_HEAP_LANES * 8, stream) != cudaSuccess ||
         cudaMemsetAsync(in->d_cur, 0, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 4, stream) != cudaSuccess ||
         cudaMemsetAsync(in->d_lsize, 0, (size_t)std::max<uint32_t>(in->npages, 1) * 4, stream) != cudaSuccess ||
         cudaMemsetAsync(in->d_fmt, 0, (size_t)c->cfg.fmt_cache * 8, stream) != cudaSuccess ||

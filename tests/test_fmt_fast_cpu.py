@@ -1,0 +1,18 @@
+"""The host printf landing pad's to_chars fast path produces the same
+characters as snprintf for every conversion it accepts."""
+import os
+import re
+import subprocess
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_fmt_fast_matches_snprintf(tmp_path):
+    exe = str(tmp_path / "fmt_check")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-I", os.path.join(ROOT, "paper_2306_11686_gb300", "csrc", "host"),
+                    os.path.join(ROOT, "tests", "host", "fmt_check.cpp"), "-o", exe], check=True, capture_output=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120).stdout
+    m = re.search(r"fmt checked (\d+) fast (\d+) mismatches (\d+)", out)
+    assert m, out
+    n, fast, bad = map(int, m.groups())
+    assert bad == 0 and fast > n // 2, out

@@ -109,6 +109,32 @@ def test_jacobi_parity(gf_lib, oracle_bin, tmp_path, n, sweeps):
     assert st.heap_live_bytes == 0
 
 
+@pytest.mark.parametrize("int_adds", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("kind", ["unit", "signed", "tiny"])
+def test_jacobi_parity_every_pipe_split(gf_lib, oracle_bin, tmp_path, int_adds, kind):
+    """Every split of the neighbour adds between the integer and FP64 pipes
+    gives the serial program's bits: on the standard grid, on a grid of mixed
+    signs (opposite-sign adds take the FP64 path) and on one scaled down to
+    the subnormal range (so does every subnormal operand)."""
+    import torch
+    gf = gf_lib
+    n, sweeps = 67, 5
+    g = inputs.jacobi_input(n, seed=9)
+    if kind == "signed":
+        g = np.where(g != 0.0, 2.0 * g - 1.0, 0.0)
+    elif kind == "tiny":
+        g = g * 2.0 ** -1060
+    inputs.write_f64(tmp_path / "in.bin", g)
+    want = oracle(oracle_bin, "jacobi", n, sweeps, tmp_path / "in.bin", tmp_path / "ref.bin")
+    with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20,
+                    heap_small_pct=5) as ctx:
+        rc, ec = ctx.run("jacobi", [n, sweeps, tmp_path / "gpu.bin", int_adds],
+                         [(torch.from_numpy(g).cuda(), gf.GF_BUF_IN)])
+    assert ec == 0
+    assert sorted(open(tmp_path / "out.txt").read().splitlines()) == sorted(want.splitlines())
+    assert (tmp_path / "gpu.bin").read_bytes() == (tmp_path / "ref.bin").read_bytes()
+
+
 @pytest.mark.parametrize("T,aggregate", [(4096 + 7, 1), (4096 + 7, 0), (1 << 20, 1)])
 def test_stress_parity(gf_lib, oracle_bin, tmp_path, T, aggregate):
     """Heap + RPC stress: line multiset and per-thread line order, per-thread

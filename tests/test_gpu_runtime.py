@@ -215,6 +215,33 @@ def test_heap_out_of_memory_returns_null(gf_lib):
     assert st.heap_fail >= 2
 
 
+def test_heap_small_class_exhaustion_and_reuse(gf_lib):
+    """Small-class exhaustion: the first pass gets every block the small heap
+    holds (then NULL, counted as failures); after all are freed the second
+    pass gets exactly the same set of blocks back, which it can only find on
+    the per-lane free stacks of other lanes and other SMs."""
+    import torch
+    gf = gf_lib
+    T, per, bytes_ = 4096, 2, 4096
+    ptrs = torch.zeros(2 * T * per, dtype=torch.int64, device="cuda")
+    with gf.Context(timeout_ns=10_000_000_000, heap_bytes=8 << 20, heap_small_pct=100) as c:
+        rc, ec = c.run("heap_exhaust", [T, per, bytes_], [(ptrs, 1)])
+        st = c.stats()
+    assert ec == 0
+    p = ptrs.cpu().numpy().view(np.uint64).reshape(2, T * per)
+    assert not (p & np.uint64(15)).any()                     # 16-byte aligned, no block flagged as shared
+    got = [set(p[k][p[k] != 0].tolist()) for k in range(2)]
+    n1 = int((p[0] != 0).sum())
+    assert len(got[0]) == n1                                  # pairwise distinct
+    slabs = (8 << 20) >> 18
+    assert (slabs - 2) * ((1 << 18) // bytes_) <= n1 <= slabs * ((1 << 18) // bytes_)
+    assert got[1] == got[0] and int((p[1] != 0).sum()) == n1  # the same blocks again, each once
+    a = np.array(sorted(got[0]), dtype=np.uint64)
+    assert (np.diff(a) >= bytes_).all()                        # no overlap
+    assert st.heap_fail == 2 * (T * per - n1)
+    assert st.heap_live_bytes == 0 and st.heap_bad_free == 0
+
+
 def test_rpc_timeout_without_server(gf_lib):
     gf = gf_lib
     with gf.Context(server_threads=0, timeout_ns=200_000_000, heap_bytes=64 << 20) as c:
@@ -230,7 +257,8 @@ def test_rpc_timeout_without_server(gf_lib):
 
 
 def test_div6_matches_ieee_division(gf_lib, ctx):
-    """gf_div6_rn (Markstein's correction) equals x / 6.0 bit for bit."""
+    """gf_div6_rn (Markstein's correction) and gf_div6_int (integer pipe)
+    equal x / 6.0 bit for bit on the GPU."""
     import torch
     rng = np.random.default_rng(6)
     n = 1 << 22
@@ -243,14 +271,57 @@ def test_div6_matches_ieee_division(gf_lib, ctx):
                         2.0 ** 1001, np.nextafter(2.0 ** 1001, 0), 1.7976931348623157e308, 6.0, 3.0, 12.0])
     x[-len(special):] = special
     x[n // 2: n // 2 + 10000] *= -1.0
-    out = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+    x[n // 2 + 10000: n // 2 + 20000] = np.ldexp(3.0 * 2.0 ** 51 + np.arange(-5000, 5000), -52)  # k switch
+    out = torch.zeros(3 * n, dtype=torch.float64, device="cuda")
     rc, ec = ctx.run("div6_probe", [n], [(torch.from_numpy(x).cuda(), 1), (out, 1)])
     assert ec == 0
-    o = out.cpu().numpy().view(np.uint64).reshape(n, 2)
+    o = out.cpu().numpy().view(np.uint64).reshape(n, 3)
     assert np.array_equal(o[:, 0], o[:, 1])
+    assert np.array_equal(o[:, 0], o[:, 2])
     ref = (x / 6.0).view(np.uint64)                              # numpy's IEEE division agrees too
     finite = np.isfinite(x)
     assert np.array_equal(o[finite, 0], ref[finite])
+
+
+def test_dadd_int_matches_fp64_add(gf_lib, ctx):
+    """gf_dadd_int (same-sign add on the integer pipe) equals the FP64 add bit
+    for bit on the GPU: every exponent gap, ties, carries, the Jacobi range,
+    zeros, subnormals, overflow, NaN/inf and random bit patterns."""
+    import torch
+    rng = np.random.default_rng(8)
+    n = 1 << 22
+    q = n // 8
+    ea = rng.integers(1, 2047, q).astype(np.uint64)
+    eb = np.maximum(ea.astype(np.int64) - rng.integers(0, 71, q), 1).astype(np.uint64)
+    frac = lambda k: rng.integers(0, 1 << 52, k, dtype=np.uint64)
+    sgn = (rng.integers(0, 2, q).astype(np.uint64) << np.uint64(63))
+    xa = sgn | (ea << np.uint64(52)) | frac(q)
+    xb = sgn | (eb << np.uint64(52)) | frac(q)
+    ties_e = rng.integers(60, 1960, q).astype(np.uint64)
+    tx = (ties_e << np.uint64(52)) | frac(q)
+    th = ((ties_e - np.uint64(53)) << np.uint64(52)) + rng.integers(-1, 2, q).astype(np.uint64)
+    ones = (ea << np.uint64(52)) | np.uint64((1 << 52) - 1)
+    x = np.concatenate([xa.view(np.float64), tx.view(np.float64), ones.view(np.float64),
+                        rng.random(q) * 6.0, rng.integers(0, 2 ** 63, q, dtype=np.uint64).view(np.float64) *
+                        np.where(rng.random(q) < 0.5, -1.0, 1.0)])
+    y = np.concatenate([xb.view(np.float64), th.view(np.float64), xb.view(np.float64) * np.sign(ones.view(np.float64)),
+                        rng.random(q) * 6.0, rng.integers(0, 2 ** 64, q, dtype=np.uint64).view(np.float64)])
+    special = np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, np.nan, 5e-324, -5e-324, 2.2250738585072014e-308,
+                        1.7976931348623157e308, float.fromhex("0x1.fffffffffffffp1022"), 2.0 ** 1023, 3.0])
+    sx, sy = np.meshgrid(special, special)
+    x = np.concatenate([x, sx.ravel()])
+    y = np.concatenate([y, sy.ravel()])
+    m = len(x)
+    out = torch.zeros(2 * m, dtype=torch.float64, device="cuda")
+    rc, ec = ctx.run("dadd_probe", [m], [(torch.from_numpy(x).cuda(), 1), (torch.from_numpy(y).cuda(), 1), (out, 1)])
+    assert ec == 0
+    o = out.cpu().numpy().reshape(m, 2)
+    nan = np.isnan(o[:, 0])
+    assert np.array_equal(np.isnan(o[:, 1]), nan)
+    assert np.array_equal(o[~nan, 0].view(np.uint64), o[~nan, 1].view(np.uint64))
+    with np.errstate(all="ignore"):
+        ref = x + y                                              # numpy's IEEE add agrees too
+    assert np.array_equal(ref[~nan].view(np.uint64), o[~nan, 0].view(np.uint64))
 
 
 @pytest.mark.parametrize("bulk", [64 << 20, 0])
