@@ -35,9 +35,8 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_OPS_PER_POINT = 7
 # DRAM bytes (read + write) of one full launch, scaled from an ncu capture of
 # 20 sweeps without the final write (profiles/jacobi_256_sweeps_ncu.md):
-# per sweep x 100 + the 128 MiB read of the final fwrite.  None until captured
-# for the current kernel.
-TRAFFIC_PER_LAUNCH = None
+# 323.8 MB per sweep x 100 + the 134.2 MB read of the final fwrite.
+TRAFFIC_PER_LAUNCH = 100 * 323_787_000 + 134_217_728
 
 
 def max_over_ranks(seconds, world, device):
@@ -192,9 +191,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--no-write", action="store_true",
                     help="the program skips its final fwrite (profiling runs that isolate the sweeps)")
-    ap.add_argument("--workload", default="jacobi", choices=["jacobi", "stress", "batch", "learned", "serve", "e1"],
+    ap.add_argument("--workload", default="jacobi", choices=["jacobi", "stress", "batch", "learned", "serve", "e1", "link", "hbm"],
                     help="jacobi = the benchmark; the others measure the RPC/heap stress, 256-loop batching, "
-                         "learned launch shapes and serving configurations")
+                         "learned launch shapes, serving, host-link peaks and single large loops")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

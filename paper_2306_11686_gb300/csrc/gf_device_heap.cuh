@@ -115,51 +115,68 @@ static __device__ uint64_t heap_steal1(gf_heap *H, uint32_t sm, uint32_t cls, ui
     return 0;
 }
 
-/* bump-allocate up to k fresh blocks for (sm, cls) into out[...] after the first `skip` members */
-static __device__ uint32_t heap_bump(gf_heap *H, uint32_t sm, uint32_t cls, uint32_t k, uint64_t *out, uint32_t mask)
+/* current-slab word of (sm, cls): slab + 1, 0 = none yet, or one of these */
+#define GF_CUR_BUSY 0xffffffffu   /* a warp is installing a fresh slab */
+#define GF_CUR_DRY 0xfffffffeu    /* no fresh slab was left */
+
+/* bump up to k - *got blocks from slab s into out[...] (lanes of *m in order) */
+__device__ __forceinline__ void bump_from(gf_heap *H, uint32_t s, uint32_t bs, uint32_t cap, uint32_t k, uint32_t *got,
+                                          uint64_t *out, uint32_t *m)
+{
+    if (*(volatile uint32_t *)&metas(H)[s].bump >= cap)   /* full: no atomic (the counter stays small) */
+        return;
+    const uint32_t want = k - *got;
+    const uint32_t old = atomicAdd(&metas(H)[s].bump, want);
+    if (old >= cap)
+        return;
+    const uint32_t take = want < cap - old ? want : cap - old;
+    for (uint32_t j = 0; j < take; j++) {
+        const uint32_t l = __ffs(*m) - 1;
+        *m &= *m - 1;
+        out[l] = H->slab_base + ((uint64_t)s << GF_SLAB_SHIFT) + (uint64_t)(old + j) * bs;
+    }
+    *got += take;
+}
+
+/*
+ * Bump-allocate up to k blocks of (sm, cls) into out[...] for the lanes of
+ * mask (in lane order) from the SM's current slab; when it is full, one warp
+ * at a time installs a fresh slab (the word goes BUSY meanwhile, so no two
+ * warps each install one and orphan the other's remainder); with no fresh
+ * slab left, from the other SMs' current slabs.  Returns the number served.
+ */
+static __device__ uint32_t heap_bump(gf_heap *H, uint32_t sm, uint32_t cls, uint32_t k, uint64_t *out, uint32_t mask,
+                                     int64_t timeout_ns)
 {
     const uint32_t bs = 16u << cls, cap = (1u << GF_SLAB_SHIFT) / bs;
     uint32_t *cur = &curs(H)[sm * GF_HEAP_NCLASS + cls];
     uint32_t got = 0;
     uint32_t m = mask;
-    for (int attempt = 0; attempt < 40 && got < k; attempt++) {
+    backoff bo(timeout_ns);
+    bool dry = false;
+    while (got < k) {
         const uint32_t s1 = *(volatile uint32_t *)cur;
-        if (s1) {
-            const uint32_t s = s1 - 1;
-            const uint32_t want = k - got;
-            const uint32_t old = atomicAdd(&metas(H)[s].bump, want);
-            if (old < cap) {
-                const uint32_t take = want < cap - old ? want : cap - old;
-                for (uint32_t j = 0; j < take; j++) {
-                    const uint32_t l = __ffs(m) - 1;
-                    m &= m - 1;
-                    out[l] = H->slab_base + ((uint64_t)s << GF_SLAB_SHIFT) + (uint64_t)(old + j) * bs;
-                }
-                got += take;
-                if (got == k)
-                    break;
-            }
+        if (s1 == GF_CUR_BUSY) {
+            if (!bo.wait())
+                break;
+            continue;
         }
-        /* current slab exhausted: take a fresh one and make it current */
+        if (s1 == GF_CUR_DRY) {
+            dry = true;
+            break;
+        }
+        if (s1) {
+            bump_from(H, s1 - 1, bs, cap, k, &got, out, &m);
+            if (got == k)
+                break;
+        }
+        /* the current slab is full (or there is none): install a fresh one */
+        if (atomicCAS(cur, s1, GF_CUR_BUSY) != s1)
+            continue;                   /* another warp changed it: use theirs */
         const uint32_t ns = atomicAdd(&H->next_slab, 1u);
         if (ns >= H->nslabs) {
-            /* no fresh slab left: bump from other SMs' current slabs of this class */
-            for (uint32_t o = 1; o < GF_MAX_SM && got < k; o++) {
-                const uint32_t t1 = *(volatile uint32_t *)&curs(H)[((sm + o) % GF_MAX_SM) * GF_HEAP_NCLASS + cls];
-                if (!t1)
-                    continue;
-                const uint32_t want = k - got;
-                const uint32_t old = atomicAdd(&metas(H)[t1 - 1].bump, want);
-                if (old >= cap)
-                    continue;
-                const uint32_t take = want < cap - old ? want : cap - old;
-                for (uint32_t j = 0; j < take; j++) {
-                    const uint32_t l = __ffs(m) - 1;
-                    m &= m - 1;
-                    out[l] = H->slab_base + ((uint64_t)(t1 - 1) << GF_SLAB_SHIFT) + (uint64_t)(old + j) * bs;
-                }
-                got += take;
-            }
+            atomicExch(cur, GF_CUR_DRY);
+            dry = true;
             break;
         }
         const uint32_t want = k - got < cap ? k - got : cap;
@@ -175,6 +192,15 @@ static __device__ uint32_t heap_bump(gf_heap *H, uint32_t sm, uint32_t cls, uint
         got += want;
         __threadfence();
         atomicExch(cur, ns + 1);
+    }
+    if (dry) {
+        /* no fresh slab left: bump from the other SMs' current slabs of this class */
+        for (uint32_t o = 1; o < GF_MAX_SM && got < k; o++) {
+            const uint32_t t1 = *(volatile uint32_t *)&curs(H)[((sm + o) % GF_MAX_SM) * GF_HEAP_NCLASS + cls];
+            if (t1 == 0 || t1 >= GF_CUR_DRY)
+                continue;
+            bump_from(H, t1 - 1, bs, cap, k, &got, out, &m);
+        }
     }
     return got;
 }
@@ -296,12 +322,12 @@ static __device__ __noinline__ void *gf_malloc(size_t n)
     uint64_t *out = gfd::s_xfer[warp];
     /* every lane: its own stack */
     uint64_t p = gfd::heap_pop1(H, sm, cls, lane);
-    /* the lanes left empty-handed: one bump of the current slab for the group */
-    const uint32_t miss = __ballot_sync(grp, p == 0) & grp;
-    if (miss) {
+    /* the lanes left empty-handed: one bump of the current slab per class */
+    const uint32_t gmiss = __ballot_sync(grp, p == 0) & grp;
+    if (gmiss) {
         if (lane == leader) {
-            const uint32_t got = gfd::heap_bump(H, sm, cls, __popc(miss), out, miss);
-            uint32_t r = miss;
+            const uint32_t got = gfd::heap_bump(H, sm, cls, __popc(gmiss), out, gmiss, S->timeout_ns);
+            uint32_t r = gmiss;
             for (uint32_t j = 0; j < got; j++)
                 r &= r - 1;
             for (; r; r &= r - 1)
@@ -325,6 +351,8 @@ static __device__ __noinline__ void *gf_malloc(size_t n)
         const unsigned long long live = atomicAdd((unsigned long long *)&H->live_bytes, bs * got) + bs * got;
         atomicMax((unsigned long long *)&H->high_water, live);
     }
+    __syncwarp(grp);                   /* the group leaves with its leader, so a following
+                                        * warp-aggregated call (printf) finds it converged */
     return (void *)p;
 }
 
@@ -375,6 +403,7 @@ static __device__ __noinline__ void gf_free(void *p)
         atomicAdd((unsigned long long *)&H->n_free, nd);
         atomicAdd((unsigned long long *)&H->live_bytes, 0ull - bs * nd);
     }
+    __syncwarp(grp);                   /* leave together, as in gf_malloc */
 }
 
 /* size of the heap block holding p (0 if p is not a live heap block start) */

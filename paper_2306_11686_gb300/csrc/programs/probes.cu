@@ -280,6 +280,70 @@ GF_MAIN(heap_exhaust)(int argc, char **argv)
     return 0;
 }
 
+/* link_probe bytes reps dir         buffers: 0 = device bytes, 1 = int64 ns[reps]
+ * Times `reps` grid-wide copies of `bytes` between device memory and the
+ * context's bulk arena (pinned host memory mapped into the device): dir 0 =
+ * device stores into host memory (the fwrite path), dir 1 = device loads
+ * from host memory (the fread path).  ns[r] = device time of copy r. */
+GF_MAIN(link_probe)(int argc, char **argv)
+{
+    if (argc < 4)
+        return 2;
+    const uint64_t bytes = (uint64_t)gf_atoll(argv[1]);
+    const int reps = (int)gf_atoll(argv[2]), dir = (int)gf_atoll(argv[3]);
+    uint8_t *dev = (uint8_t *)gf_buffer(0);
+    long long *ns = (long long *)gf_buffer(1);
+    uint8_t *host = (uint8_t *)gfd::s_st->bulk_dev;
+    if (!dev || !ns || !host || bytes > gfd::s_st->bulk_bytes || gf_buffer_bytes(0) < bytes ||
+        gf_buffer_bytes(1) < (uint64_t)reps * 8)
+        return 2;
+    for (int r = 0; r < reps; r++) {
+        const uint64_t t0 = gfd::now_ns();
+        const int rc = dir == 0 ? gfd::copy_region(host, dev, bytes) : gfd::copy_region(dev, host, bytes);
+        ns[r] = (long long)(gfd::now_ns() - t0);
+        if (rc)
+            return 10;
+    }
+    return 0;
+}
+
+/* rpc_latency n mode                buffers: 0 = int64 ns[n]
+ * One thread makes n RPCs in a row, each timed on the device: mode 0 =
+ * clock() (an empty round trip), mode 1 = fprintf(f, "fread reads: %s\n",
+ * buffer) with a 128-byte buffer and f = /dev/null -- the call the paper
+ * times 1000 times for its RPC cost breakdown (Sec. 5, "RPC Performance"). */
+GF_MAIN(rpc_latency)(int argc, char **argv)
+{
+    if (argc < 3)
+        return 2;
+    const long long n = gf_atoll(argv[1]);
+    const int mode = (int)gf_atoll(argv[2]);
+    long long *ns = (long long *)gf_buffer(0);
+    if (n < 1 || !ns || gf_buffer_bytes(0) < (uint64_t)n * 8)
+        return 2;
+    char *buf = (char *)gf_malloc(128);
+    if (!buf)
+        return 4;
+    for (int k = 0; k < 127; k++)
+        buf[k] = (char)('a' + k % 26);
+    buf[127] = 0;
+    GF_FILE f = mode ? gf_fopen("/dev/null", "w") : (GF_FILE)0;
+    if (mode && !f)
+        return 3;
+    for (long long k = 0; k < n; k++) {
+        const uint64_t t0 = gfd::now_ns();
+        if (mode)
+            gf_fprintf(f, "fread reads: %s\n", buf);
+        else
+            gf_clock();
+        ns[k] = (long long)(gfd::now_ns() - t0);
+    }
+    if (f)
+        gf_fclose(f);
+    gf_free(buf);
+    return 0;
+}
+
 /* rpc_timeout                      the host does not serve: the call must come back with GF_ETIMEDOUT */
 GF_MAIN(rpc_timeout)(int argc, char **argv)
 {

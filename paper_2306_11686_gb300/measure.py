@@ -12,7 +12,12 @@ Each function prints one JSON line with its own metric:
            runtime's fixed shape;
   serve    64 served programs (CSR SpMV, 1M rows, 16 nnz/row, 10 passes,
            ~64 libc requests per pass) under continuous batching: calls/s,
-           RPC p50/p99, admission -> done latency, SpMV GB/s.
+           RPC p50/p99, admission -> done latency, SpMV GB/s;
+  link     the host link's measured peaks, the denominators of the RPC and
+           bulk-I/O figures: pinned cudaMemcpy H2D/D2H and grid-wide device
+           stores/loads of mapped host memory for 64 B .. 64 MiB, and the
+           single-thread RPC round trip (empty call; the paper's 128-byte
+           fprintf experiment).
 """
 from __future__ import annotations
 
@@ -175,5 +180,99 @@ def e1(args):
     print(json.dumps(line))
 
 
+def link(args):
+    import torch
+    sizes = [64 << (2 * k) for k in range(11)]                  # 64 B .. 64 MiB
+    big = sizes[-1]
+    dev = torch.zeros(big, dtype=torch.uint8, device="cuda")
+    host = torch.zeros(big, dtype=torch.uint8).pin_memory()
+    stream = torch.cuda.Stream()
+    table = {}
+    for n in sizes:
+        reps = 200 if n <= (1 << 20) else 20
+        for name, dst, src in (("memcpy_h2d", dev[:n], host[:n]), ("memcpy_d2h", host[:n], dev[:n])):
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    dst.copy_(src, non_blocking=True)
+                e0, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    dst.copy_(src, non_blocking=True)
+                e1_.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1_) / 1e3 / reps
+            table[f"{name}/{n}"] = {"us": round(t * 1e6, 3), "GBps": round(n / t / 1e9, 3)}
+    reps = 20
+    ns = torch.zeros(max(reps, 1000), dtype=torch.int64, device="cuda")
+    with gf.Context(bulk_bytes=big, heap_bytes=64 << 20, timeout_ns=int(60e9), stdout_path=os.devnull) as ctx:
+        for n in sizes:
+            for d, name in ((0, "device_store_mapped"), (1, "device_load_mapped")):
+                rc, ec = ctx.run("link_probe", [n, reps, d], [(dev, 1), (ns, 1)])
+                if ec != 0:
+                    raise RuntimeError(f"link_probe exit {ec}")
+                t = float(np.median(ns[1:reps].cpu().numpy())) / 1e9
+                table[f"{name}/{n}"] = {"us": round(t * 1e6, 3), "GBps": round(n / t / 1e9, 3)}
+        rtt = {}
+        for mode, name in ((0, "clock"), (1, "fprintf_128B")):
+            rc, ec = ctx.run("rpc_latency", [1000, mode], [(ns, 1)])
+            if ec != 0:
+                raise RuntimeError(f"rpc_latency exit {ec}")
+            v = ns[:1000].cpu().numpy().astype(np.float64) / 1e3
+            rtt[name] = {"mean_us": round(float(v.mean()), 3), "p50_us": round(float(np.median(v)), 3),
+                         "p99_us": round(float(np.percentile(v, 99)), 3), "calls_per_s": round(1e6 / v.mean())}
+    peak = {k: max(v["GBps"] for kk, v in table.items() if kk.startswith(k + "/"))
+            for k in ("memcpy_h2d", "memcpy_d2h", "device_store_mapped", "device_load_mapped")}
+    line = {"metric": "host link GB/s and RPC round trip", "value": peak["device_store_mapped"], "unit": "GB/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "bytes", "data": "synthetic",
+            "config": {"workload": "message sizes 64 B .. 64 MiB; 1000 single-thread RPCs per kind"},
+            "detail": {"peak_GBps": peak, "single_thread_rpc": rtt, "table": table}}
+    print(json.dumps(line))
+
+
+def hbm(args):
+    """One large legacy loop through the plain runtime (one static chunk-1
+    parallel region, z = a x + y, 24 B per iteration) at N = 2^26 and 2^28:
+    inputs far larger than L2, so the region's GB/s is HBM bandwidth."""
+    import torch
+    peak = None
+    try:
+        with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+    except Exception:
+        pass
+    res = {}
+    stream = torch.cuda.Stream()
+    for lg in (26, 28):
+        n = 1 << lg
+        x = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+        y = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+        z = torch.zeros(n, dtype=torch.float64, device="cuda")
+        i64 = lambda v: torch.tensor(v, dtype=torch.int64, device="cuda")
+        bufs = [(i64([n]), 1), (torch.tensor([2.5], dtype=torch.float64, device="cuda"), 1), (i64([0]), 1),
+                (x, 1), (y, 1), (z, 1),
+                (torch.zeros(2, dtype=torch.int64, device="cuda"), 1)]
+        with gf.Context(stream=stream, heap_bytes=64 << 20, timeout_ns=int(60e9)) as ctx:
+            _timed_run(ctx, stream, "loops", [0, 1, 1, 0], bufs)
+            ts = []
+            for _ in range(5):
+                _timed_run(ctx, stream, "loops", [0, 1, 1, 0], bufs)
+                st = ctx.stats()
+                ts.append(st.region_ns / max(1, st.regions) / 1e9)
+        ok = bool(torch.equal(z, 2.5 * x + y))
+        t = min(ts)
+        res[f"2^{lg}"] = {"region_s": t, "GBps": 24 * n / t / 1e9, "bytes": 24 * n, "correct": ok}
+        del x, y, z
+    best = max(v["GBps"] for v in res.values())
+    line = {"metric": "loop GB/s (% HBM peak)", "value": round(best, 1), "unit": "GB/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "one axpy loop z = 2.5 x + y, N = 2^26 and 2^28, static chunk 1, "
+                                   "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": round(best, 1), "peak": peak, "unit": "GB/s",
+                         "frac": None if not peak else round(best / peak, 4), "peak_kind": "measured"},
+            "detail": res}
+    print(json.dumps(line))
+
+
 def run(args):
-    {"stress": stress, "batch": batch, "learned": learned, "serve": serve_run, "e1": e1}[args.workload](args)
+    {"stress": stress, "batch": batch, "learned": learned, "serve": serve_run, "e1": e1,
+     "link": link, "hbm": hbm}[args.workload](args)
