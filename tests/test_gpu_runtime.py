@@ -335,3 +335,32 @@ def test_fwrite_append_mode_in_order(gf_lib, tmp_path, bulk):
         rc, ec = c.run("fwrite_modes", [tmp_path / "a.bin", n], [(torch.from_numpy(data).cuda(), 1)])
     assert ec == 0
     assert (tmp_path / "a.bin").read_bytes() == b"head" + data.tobytes() * 2
+
+
+def test_link_probe_round_trip_and_rpc_latency(gf_lib, tmp_path):
+    """The host-link probe moves the bytes it times: device -> mapped host
+    arena -> device restores a pattern exactly (sizes off the 16-byte path
+    too); the single-thread RPC timer reports one positive time per call."""
+    import torch
+    gf = gf_lib
+    pat = torch.from_numpy(np.frombuffer(np.random.default_rng(4).bytes(1 << 20), dtype=np.uint8).copy()).cuda()
+    ns = torch.zeros(64, dtype=torch.int64, device="cuda")
+    with gf.Context(timeout_ns=10_000_000_000, heap_bytes=64 << 20, bulk_bytes=1 << 20,
+                    stdout_path=tmp_path / "out.txt") as c:
+        for n in (64, 1000, 4096, (1 << 20) - 3, 1 << 20):
+            dev = pat.clone()
+            rc, ec = c.run("link_probe", [n, 2, 0], [(dev, 1), (ns, 1)])       # device -> host arena
+            assert ec == 0 and (ns[:2] > 0).all()
+            dev[:n] = 0
+            rc, ec = c.run("link_probe", [n, 2, 1], [(dev, 1), (ns, 1)])       # host arena -> device
+            assert ec == 0
+            assert torch.equal(dev, pat), n
+        rc, ec = c.run("link_probe", [(1 << 20) + 16, 1, 0], [(pat, 1), (ns, 1)])
+        assert ec == 2                                                       # larger than the arena: refused
+        for mode in (0, 1):
+            ns.zero_()
+            rc, ec = c.run("rpc_latency", [50, mode], [(ns, 1)])
+            assert ec == 0
+            v = ns[:50].cpu().numpy()
+            assert (v > 0).all() and (v < 10_000_000_000).all()
+            assert (ns[50:].cpu().numpy() == 0).all()
