@@ -67,6 +67,16 @@ typedef struct gf_config {
     int32_t device;               /* CUDA device ordinal (-1 = current device)                    */
     uint64_t bulk_bytes;          /* pinned, device-mapped staging arena per instance for large
                                      fwrite/fread from the serial part (default 64 MiB; 0 = DMA) */
+    uint32_t split_regions;       /* 0 (default): regions run on the program's persistent grid.
+                                     1: the paper's kernel split (Sec. 3.3, Fig. 3), kept as a
+                                     comparator -- the program kernel is one block, and each
+                                     parallel region is an RPC on which the host server launches
+                                     the region as its own kernel (on a stream of the instance)
+                                     while the initial thread waits for its blocks to finish.
+                                     Needs server_threads >= 1.  A region kernel cannot start
+                                     under a profiler that serialises kernels (ncu): the program
+                                     then times out waiting for it. */
+    uint32_t pad0;
 } gf_config;
 
 /* A buffer mapped into the program before main (the loader's job, paper

@@ -56,6 +56,10 @@ __shared__ gf_state *s_st;                 /* this program's state              
 __shared__ uint32_t s_epoch;               /* epoch seen by this block's poller         */
 __shared__ uint32_t s_last;                /* this block combines the reduction         */
 __shared__ uint32_t s_abort;               /* this block's workers give up (idle bound) */
+__shared__ uint32_t s_kr;                  /* 1 outside a program's persistent kernel (a
+                                              region kernel of the split, a standalone
+                                              kernel): every thread is a worker, none is
+                                              the initial thread, ids have no offset   */
 __shared__ uint64_t s_red[GF_MAX_WARPS][2];/* per-warp reduction partials               */
 __shared__ uint64_t s_xfer[GF_MAX_WARPS][32]; /* per-warp lane hand-off (heap, rpc)    */
 
@@ -115,7 +119,7 @@ __device__ __forceinline__ uint32_t smid()
 }
 
 __device__ __forceinline__ gf_state *st() { return s_st; }
-__device__ __forceinline__ bool is_initial_thread() { return blockIdx.x == 0 && threadIdx.x == 0; }
+__device__ __forceinline__ bool is_initial_thread() { return blockIdx.x == 0 && threadIdx.x == 0 && !s_kr; }
 
 __device__ __forceinline__ void set_error(int e)
 {
@@ -148,6 +152,14 @@ struct wctx {
 __device__ __forceinline__ wctx make_wctx()
 {
     wctx w;
+    if (s_kr) {                 /* region kernel: every thread of every block is a worker */
+        w.tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        w.nthreads = (int64_t)gridDim.x * blockDim.x;
+        w.nbar = blockDim.x;
+        w.wfirst = 0;
+        w.poller = threadIdx.x == 0;
+        return w;
+    }
     const bool b0 = blockIdx.x == 0;
     w.tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - 32;
     w.nthreads = (int64_t)gridDim.x * blockDim.x - 32;
@@ -168,13 +180,13 @@ __device__ __forceinline__ int64_t gf_thread_num()
 {
     if (gfd::is_initial_thread())
         return 0;
-    return (int64_t)blockIdx.x * blockDim.x + threadIdx.x - 32;
+    return (int64_t)blockIdx.x * blockDim.x + threadIdx.x - (gfd::s_kr ? 0 : 32);
 }
 __device__ __forceinline__ int64_t gf_num_threads()
 {
     if (gfd::is_initial_thread())
         return 1;
-    return (int64_t)gridDim.x * blockDim.x - 32;
+    return (int64_t)gridDim.x * blockDim.x - (gfd::s_kr ? 0 : 32);
 }
 
 /* ====================================================================== reductions */
@@ -301,7 +313,7 @@ template <class A> __device__ void finish_reduce(A a, const wctx &w)
             part[1] = wd[1];
             __threadfence();
             uint32_t t = atomicAdd(&S->red_ticket, 1u);
-            s_last = (t == S->nblocks - 1) ? 1u : 0u;
+            s_last = (t == gridDim.x - 1) ? 1u : 0u;
         }
     }
     bar_workers(w.nbar);
@@ -310,7 +322,7 @@ template <class A> __device__ void finish_reduce(A a, const wctx &w)
         const uint64_t *part = (const uint64_t *)S->partials;
         A c;
         const uint32_t idx = threadIdx.x - w.wfirst * 32;
-        for (uint32_t k = idx; k < S->nblocks; k += w.nbar) {
+        for (uint32_t k = idx; k < gridDim.x; k += w.nbar) {
             A p;
             uint64_t wd[2] = {ld_vol64(part + 2 * k), ld_vol64(part + 2 * k + 1)};
             p.from_words(wd);
@@ -389,11 +401,42 @@ template <class T, int OP, class F> __device__ void tramp_reduce(const gf_region
 }
 
 /* ------------------------------------------------------------ region launch (initial thread) */
+/* kernel split: ask the host to launch the region kernel; its grid, or < 0 */
+static __device__ int64_t split_launch(gf_state *S, int *status);
+
 static __device__ __noinline__ int run_region(gf_state *S)
 {
     if (*(volatile int32_t *)&S->error)      /* after a timeout the workers may still be busy */
         return S->error;
     S->st_regions++;
+    if (S->split) {
+        /* the paper's kernel split (Sec. 3.3, Fig. 3): one RPC per region, on
+         * which the host launches the region as its own kernel; the initial
+         * thread then waits for that kernel's blocks to finish */
+        S->dyn_next = 0;
+        S->red_ticket = 0;
+        const uint64_t t0 = now_ns();
+        __threadfence();
+        int st = GF_OK;
+        const int64_t grid = split_launch(S, &st);
+        if (st != GF_OK || grid <= 0) {
+            set_error(st != GF_OK ? st : GF_ECUDA);
+            return S->error;
+        }
+        const uint32_t target = S->done_target + (uint32_t)grid;
+        S->done_target = target;
+        backoff bo(S->timeout_ns);
+        while ((int32_t)(ld_acq_gpu(&S->done_blocks) - target) < 0) {
+            if (now_ns() - t0 < GF_REGION_SPIN_NS)
+                continue;
+            if (!bo.wait()) {
+                set_error(GF_ETIMEDOUT);
+                return GF_ETIMEDOUT;
+            }
+        }
+        S->st_region_ns += now_ns() - t0;
+        return GF_OK;
+    }
     const uint32_t target = S->done_target + S->nblocks;
     S->done_target = target;
     S->dyn_next = 0;
@@ -634,7 +677,7 @@ static __device__ __noinline__ int gf_barrier()
         s_rc = GF_OK;
         const uint32_t gen = *(volatile uint32_t *)&S->bar_gen;
         __threadfence();
-        if (atomicAdd(&S->bar_count, 1u) == S->nblocks - 1) {
+        if (atomicAdd(&S->bar_count, 1u) == gridDim.x - 1) {
             S->bar_count = 0;
             __threadfence();
             gfd::st_rel_gpu(&S->bar_gen, gen + 1);
@@ -700,8 +743,10 @@ typedef int (*main_t)(int, char **);
 template <main_t MAIN, int MINB = GF_MIN_BLOCKS>
 __global__ void __launch_bounds__(GF_BLOCK, MINB) program_kernel(gf_state *S, int argc, char **argv)
 {
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         s_st = S;
+        s_kr = 0;
+    }
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x < 32) {
         if (threadIdx.x == 0) {
@@ -717,6 +762,35 @@ __global__ void __launch_bounds__(GF_BLOCK, MINB) program_kernel(gf_state *S, in
         return;
     }
     worker_loop(S);
+}
+
+/*
+ * The kernel split's region kernel (paper Sec. 3.3, Fig. 3), a comparator:
+ * with split_regions the host server launches it for each parallel region of
+ * the program.  Every thread of every block is a worker; the published region
+ * runs through its trampoline, and each block counts itself in done_blocks,
+ * which the initial thread waits on.  Instantiated per program, because the
+ * trampoline pointers are valid only in the program's own module.
+ */
+template <main_t MAIN, int MINB = GF_MIN_BLOCKS>
+__global__ void __launch_bounds__(GF_BLOCK, MINB) region_kernel(gf_state *S)
+{
+    if (threadIdx.x == 0) {
+        s_st = S;
+        s_kr = 1;
+        s_abort = *(volatile int32_t *)&S->error != 0;   /* one reading for the whole block */
+    }
+    __syncthreads();
+    if (!s_abort) {
+        const wctx w = make_wctx();
+        tramp_t fn = (tramp_t)S->region.fn;
+        fn(&S->region, w);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&S->done_blocks, 1u);
+    }
 }
 
 } // namespace gfd
@@ -739,7 +813,19 @@ __global__ void __launch_bounds__(GF_BLOCK, MINB) program_kernel(gf_state *S, in
             return -1;                                                                         \
         return n;                                                                              \
     }                                                                                          \
-    static const int gf_reg_##name = gf_program_register(#name, gf_launch_##name, gf_occ_##name); \
+    /* grid 0: only load the region kernel (before the program kernel runs:     \
+     * a lazily loaded kernel would wait for the running program to end) */    \
+    static cudaError_t gf_region_##name(void **args, unsigned grid, unsigned block, void *stream) \
+    {                                                                                          \
+        if (!grid) {                                                                           \
+            cudaFuncAttributes fa;                                                             \
+            return cudaFuncGetAttributes(&fa, (const void *)&gfd::region_kernel<gf_main_##name, minb>); \
+        }                                                                                      \
+        return cudaLaunchKernel((const void *)&gfd::region_kernel<gf_main_##name, minb>, dim3(grid), \
+                                dim3(block), args, 0, (cudaStream_t)stream);                   \
+    }                                                                                          \
+    static const int gf_reg_##name =                                                           \
+        gf_program_register(#name, gf_launch_##name, gf_occ_##name, gf_region_##name);        \
     __device__ int gf_main_##name
 
 /* GF_MAIN(name)(int argc, char **argv) { ... } defines and registers a program */

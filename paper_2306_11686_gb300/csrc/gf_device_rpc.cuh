@@ -365,6 +365,13 @@ template <class... A> __device__ inline int64_t rpc(uint32_t op, const char *fmt
     return rpc_issue(op, fmt, a, status);
 }
 
+/* the kernel split: the host launches this region as its own kernel and
+ * answers with the kernel's grid (declared next to run_region) */
+static __device__ int64_t split_launch(gf_state *S, int *status)
+{
+    return rpc(GF_OP_REGION, nullptr, status, (unsigned long long)S->prog_id);
+}
+
 /* Single-lane asynchronous call for the initial thread: post a slot now,
  * collect its return later, so the grid can work while the host does. */
 static __device__ __noinline__ int rpc_post1(uint32_t op, const argpack &a, unsigned long long *tk)

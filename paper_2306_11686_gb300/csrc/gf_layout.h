@@ -40,6 +40,7 @@ enum gf_opcode {
     GF_OP_FREAD = 7,      /* (buf, size, nmemb, FILE*) -> items read, bytes written back  */
     GF_OP_FFLUSH = 8,     /* (FILE*) -> 0 / EOF                                           */
     GF_OP_STRTOD = 9,     /* (str, int64 *used) -> bits of strtod(str), chars consumed    */
+    GF_OP_REGION = 10,    /* (instance) -> grid of the region kernel the host launched     */
     GF_OP_USER = 256      /* first opcode for handlers registered with gf_rpc_register    */
 };
 
@@ -171,6 +172,7 @@ typedef struct gf_state {
     uint64_t buf_ptr[GF_MAX_BUFS];
     uint64_t buf_bytes[GF_MAX_BUFS];
     uint32_t nbufs;
+    uint32_t split;            /* 1: regions run as host-launched kernels (the paper's split) */
     /* results written by the device */
     int32_t exit_code, error, main_done;
     uint64_t st_calls[GF_NSTAT];  /* RPC calls per opcode (lane records)              */

@@ -471,6 +471,12 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
     }
     case GF_OP_CLOCK:
         return (int64_t)clock();
+    case GF_OP_REGION:
+        /* the kernel split: launch the region, answer at once (the device
+         * waits for the kernel's blocks; a server thread never blocks here) */
+        if (!region_)
+            return -1;
+        return region_(seg ? seg->prog : (r.nargs ? (uint32_t)r.word(0) : 0u));
     case GF_OP_STRTOD: {
         /* the device's slow path: exact conversion by the host libc */
         if (r.nargs < 2 || r.tag(0) != GF_T_STR || r.tag(1) != GF_T_BLOB_W || r.blob_len(1) < 8)

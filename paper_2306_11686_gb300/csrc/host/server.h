@@ -63,6 +63,8 @@ typedef std::function<uint64_t(void *buf, uint64_t want)> source_fn;
 typedef std::function<uint64_t(uint64_t dev_dst, uint64_t bytes, const source_fn &src)> h2d_fn;
 /* returns a device-readable address of a stable copy of s (getenv interning) */
 typedef std::function<uint64_t(const std::string &s)> intern_fn;
+/* launches instance `idx`'s region kernel (kernel split); its grid, or < 0 */
+typedef std::function<int64_t(uint32_t idx)> region_fn;
 typedef int64_t (*user_fn)(void *user, uint32_t opcode, void *rec);
 
 struct HostStats {
@@ -82,6 +84,7 @@ class Server {
     void set_stdout(FILE *f);
     void set_dma(d2h_fn d2h, h2d_fn h2d);
     void set_intern(intern_fn f) { intern_ = f; }
+    void set_region(region_fn f) { region_ = f; }
     int register_user(uint32_t opcode, user_fn fn, void *user);
 
     /* serve every published slot of `seg` that belongs to server thread `tid`
@@ -106,6 +109,7 @@ class Server {
     std::set<uint64_t> files_;
     d2h_fn d2h_;
     h2d_fn h2d_;
+    region_fn region_;
     intern_fn intern_;
     std::mutex intern_mu_;
     std::map<std::string, uint64_t> interned_;

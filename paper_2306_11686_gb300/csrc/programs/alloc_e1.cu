@@ -21,8 +21,10 @@ __global__ void __launch_bounds__(256) e1_kernel(gf_state *S, gfpa::balanced B, 
                                                  unsigned long long *fails)
 {
     if (KIND == 0) {
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             gfd::s_st = S;
+            gfd::s_kr = 1;      /* not a program kernel: every thread is a worker */
+        }
         __syncthreads();
     }
     const unsigned long long tag = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x + 1;

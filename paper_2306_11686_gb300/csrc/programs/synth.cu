@@ -39,8 +39,10 @@ static __device__ __forceinline__ uint64_t synth_mix(uint64_t z)
 __global__ void __launch_bounds__(1024) synth_kernel(SynthP P, const double *__restrict__ x, double *__restrict__ z,
                                                      gf_state *S, unsigned long long *counter)
 {
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         gfd::s_st = S;
+        gfd::s_kr = 1;          /* not a program kernel: every thread is a worker */
+    }
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;
     const int64_t items = (P.trip + P.chunk - 1) / P.chunk;

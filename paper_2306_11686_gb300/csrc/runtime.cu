@@ -47,6 +47,7 @@ struct ProgEntry {
     std::string name;
     gf_launch_fn launch;
     gf_occ_fn occ;
+    gf_launch_fn region;    /* the program's region kernel (kernel split) */
 };
 static std::mutex &reg_mu()
 {
@@ -60,10 +61,10 @@ static std::vector<ProgEntry> &registry()
 }
 
 extern "C" __attribute__((visibility("default"))) int gf_program_register(const char *name, gf_launch_fn launch,
-                                                                           gf_occ_fn occ)
+                                                                           gf_occ_fn occ, gf_launch_fn region)
 {
     std::lock_guard<std::mutex> g(reg_mu());
-    registry().push_back({name, launch, occ});
+    registry().push_back({name, launch, occ, region});
     return (int)registry().size() - 1;
 }
 
@@ -95,6 +96,10 @@ struct Instance {
     uint64_t h_ext0 = 0;
     gfh::Segment seg;
     cudaEvent_t ev_done = nullptr;
+    /* kernel split: the running program's region kernel, its grid and stream */
+    gf_launch_fn region = nullptr;
+    uint32_t region_grid = 0;
+    cudaStream_t region_stream = nullptr;
 };
 
 struct gf_handle {
@@ -165,6 +170,8 @@ extern "C" GF_API void gf_config_default(gf_config *c)
     c->stdout_path = nullptr;
     c->fmt_cache = 4096;
     c->bulk_bytes = 64ull << 20;
+    c->split_regions = 0;
+    c->pad0 = 0;
     c->device = -1;
 }
 
@@ -331,6 +338,8 @@ static int inst_alloc(gf_ctx *c, Instance *in)
     GF_CK(cudaMalloc(&in->d_ext, (size_t)GF_LARGE_EXT_MAX * 8));
     GF_CK(cudaMalloc(&in->d_lsize, (size_t)std::max<uint32_t>(in->npages, 1) * 4));
     GF_CK(cudaEventCreateWithFlags(&in->ev_done, cudaEventDisableTiming));
+    if (cf.split_regions)
+        GF_CK(cudaStreamCreateWithFlags(&in->region_stream, cudaStreamNonBlocking));
     in->seg.nslots = cf.ring_slots;
     in->seg.slot_bytes = cf.slot_bytes;
     in->seg.prog = (uint32_t)in->idx;
@@ -364,6 +373,8 @@ static void inst_free(Instance *in)
     cudaFree(in->d_lsize);
     if (in->ev_done)
         cudaEventDestroy(in->ev_done);
+    if (in->region_stream)
+        cudaStreamDestroy(in->region_stream);
 }
 
 extern "C" GF_API int gf_finalize(gf_ctx *c)
@@ -417,6 +428,8 @@ extern "C" GF_API int gf_init(const gf_config *cfg, gf_ctx **out)
         return GF_EINVAL;
     if (cf.server_threads && (!pow2(cf.server_threads) || cf.server_threads > cf.ring_slots))
         return GF_EINVAL;
+    if (cf.split_regions > 1 || (cf.split_regions && cf.server_threads == 0))
+        return GF_EINVAL;                /* the split needs a server thread to launch regions */
     gf_ctx *c = new gf_ctx();
     c->cfg = cf;
     memset(&c->last, 0, sizeof c->last);
@@ -479,6 +492,19 @@ extern "C" GF_API int gf_init(const gf_config *cfg, gf_ctx **out)
     c->server.set_stdout(c->out);
     c->server.set_dma([c](uint64_t d, uint64_t n, const gfh::sink_fn &s, bool par) { return dma_d2h(c, d, n, s, par); },
                       [c](uint64_t d, uint64_t n, const gfh::source_fn &s) { return dma_h2d(c, d, n, s); });
+    /* kernel split: launch the running program's region kernel on its instance's
+     * stream and answer with the grid; the device waits for its blocks */
+    c->server.set_region([c](uint32_t idx) -> int64_t {
+        if (idx >= c->inst.size())
+            return -1;
+        Instance *in = c->inst[idx];
+        if (!in->region || !in->region_grid || !in->region_stream)
+            return -1;
+        gf_state *a_state = in->d_state;
+        void *args[1] = {&a_state};
+        const cudaError_t e = in->region(args, in->region_grid, GF_BLOCK_THREADS, in->region_stream);
+        return e == cudaSuccess ? (int64_t)in->region_grid : -1;
+    });
     c->server.set_intern([c](const std::string &s) -> uint64_t {
         if (c->intern_used + s.size() + 1 > GF_INTERN_BYTES)
             return 0;
@@ -575,6 +601,17 @@ extern "C" GF_API int gf_launch(gf_ctx *c, gf_program prog, int argc, const char
         grid = c->cfg.grid ? c->cfg.grid : std::max<uint32_t>(1, full / c->cfg.max_programs);
     if (grid > full || grid > (uint32_t)c->nsm * GF_MAX_BLOCKS_PER_SM)
         return GF_EINVAL;
+    /* kernel split: the program kernel is one block (the initial thread's);
+     * regions get the grid, less the block the program kernel holds */
+    uint32_t region_grid = 0;
+    if (c->cfg.split_regions) {
+        region_grid = std::max<uint32_t>(1, grid >= full ? full - 1 : grid);
+        grid = 1;
+        /* load the region kernel now: with lazy loading its first launch
+         * would otherwise wait for the running program kernel to finish */
+        if (!pe.region || pe.region(nullptr, 0, 0, nullptr) != cudaSuccess)
+            return GF_ECUDA;
+    }
     /* argv block: pointer array then strings, all device addresses */
     size_t need = (size_t)(argc + 1) * 8;
     for (int k = 0; k < argc; k++)
@@ -598,6 +635,8 @@ extern "C" GF_API int gf_launch(gf_ctx *c, gf_program prog, int argc, const char
     h->stream = (cudaStream_t)(stream ? stream : (c->cfg.stream ? c->cfg.stream : c->own_stream));
     h->grid = grid;
     h->block = GF_BLOCK_THREADS;
+    in->region = pe.region;
+    in->region_grid = region_grid;
     auto bail = [&](int e) {
         release_staged(h, false);
         in->busy = false;
@@ -677,6 +716,7 @@ static int inst_start(gf_ctx *c, Instance *in, cudaStream_t stream, uint32_t gri
     s.partials = (uint64_t)in->d_partials;
     s.bulk_dev = in->bulk_dev;
     s.bulk_bytes = in->bulk_host ? c->cfg.bulk_bytes : 0;
+    s.split = c->cfg.split_regions ? 1u : 0u;
     gf_heap &H = s.heap;
     H.base = (uint64_t)in->d_heap;
     H.bytes = in->slab_bytes + in->large_bytes;

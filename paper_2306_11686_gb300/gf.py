@@ -20,6 +20,7 @@ GF_OK, GF_EINVAL, GF_ENOMEM, GF_ERING, GF_ETIMEDOUT, GF_EHOST, GF_ECUDA, GF_ENOE
 GF_BUF_IN, GF_BUF_OUT = 1, 2
 SCHED_STATIC, SCHED_DYNAMIC = 0, 1
 OP_PRINTF, OP_FOPEN, OP_FWRITE, OP_FCLOSE, OP_CLOCK, OP_GETENV, OP_FREAD, OP_FFLUSH = 1, 2, 3, 4, 5, 6, 7, 8
+OP_STRTOD, OP_REGION = 9, 10
 NOPS = 16
 
 
@@ -39,6 +40,8 @@ class gf_config(ctypes.Structure):
         ("fmt_cache", ctypes.c_uint32),
         ("device", ctypes.c_int32),
         ("bulk_bytes", ctypes.c_uint64),
+        ("split_regions", ctypes.c_uint32),
+        ("pad0", ctypes.c_uint32),
     ]
 
 

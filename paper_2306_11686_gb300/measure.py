@@ -13,6 +13,9 @@ Each function prints one JSON line with its own metric:
   serve    64 served programs (CSR SpMV, 1M rows, 16 nnz/row, 10 passes,
            ~64 libc requests per pass) under continuous batching: calls/s,
            RPC p50/p99, admission -> done latency, SpMV GB/s;
+  split    the persistent grid against the paper's kernel split (one RPC and
+           one host-launched kernel per region): a 64-byte region, config 1's
+           axpy program, the 256 per-loop regions, Jacobi 256^3 x 100;
   link     the host link's measured peaks, the denominators of the RPC and
            bulk-I/O figures: pinned cudaMemcpy H2D/D2H and grid-wide device
            stores/loads of mapped host memory for 64 B .. 64 MiB, and the
@@ -273,6 +276,64 @@ def hbm(args):
     print(json.dumps(line))
 
 
+def split(args):
+    import torch
+    tmp = tempfile.mkdtemp(prefix="gfsplit", dir=args.out_dir)
+    stream = torch.cuda.Stream()
+    res = {"persistent": {}, "split": {}}
+    dev = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    ns = torch.zeros(400, dtype=torch.int64, device="cuda")
+    n1 = 1 << 20
+    x1, y1 = inputs.axpy_inputs(n1, seed=1)
+    x1d, y1d = torch.from_numpy(x1).cuda(), torch.from_numpy(y1).cuda()
+    trips, a, off, x, y = inputs.loops_inputs()
+    nl, total = len(trips), int(trips.sum())
+    dv = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()
+    lb = [dv(trips), dv(a), dv(off), dv(x), dv(y), torch.zeros(total, dtype=torch.float64, device="cuda"),
+          torch.zeros(nl + 1, dtype=torch.int64, device="cuda")]
+    g = torch.from_numpy(inputs.jacobi_input(256, seed=2)).cuda()
+    for mode in ("persistent", "split"):
+        r = res[mode]
+        kw = dict(split_regions=1 if mode == "split" else 0, stream=stream, timeout_ns=int(60e9),
+                  stdout_path=os.path.join(tmp, f"out_{mode}.txt"))
+        with gf.Context(bulk_bytes=1 << 20, heap_bytes=64 << 20, **kw) as ctx:
+            rc, ec = ctx.run("link_probe", [64, 400, 0], [(dev, 1), (ns, 1)])
+            v = ns[10:].cpu().numpy().astype(np.float64) / 1e3
+            r["region_64B_us"] = {"p50": round(float(np.median(v)), 2), "min": round(float(v.min()), 2)}
+            y1c = y1d.clone()
+            _timed_run(ctx, stream, "axpy_sum", [n1, os.path.join(tmp, "axpy.bin")], [(x1d, 1), (y1c, 1)])
+            y1c = y1d.clone()
+            t = _timed_run(ctx, stream, "axpy_sum", [n1, os.path.join(tmp, "axpy.bin")], [(x1d, 1), (y1c, 1)])
+            r["axpy_sum_2^20_ms"] = round(t * 1e3, 3)
+            bufs = [(b, 1) for b in lb]
+            _timed_run(ctx, stream, "loops", [0, nl, 1, 0], bufs)
+            t = _timed_run(ctx, stream, "loops", [0, nl, 1, 0], bufs)
+            st = ctx.stats()
+            r["loops_256_regions"] = {"program_ms": round(t * 1e3, 3), "GBps": round(24 * total / t / 1e9, 1)}
+        with gf.Context(heap_bytes=3 * 256 ** 3 * 8 + (256 << 20), heap_small_pct=5, **kw) as ctx:
+            _timed_run(ctx, stream, "jacobi", [256, 100, "-"], [(g, gf.GF_BUF_IN)])
+            t = _timed_run(ctx, stream, "jacobi", [256, 100, "-"], [(g, gf.GF_BUF_IN)])
+            st = ctx.stats()
+            r["jacobi_256x100_ms"] = round(t * 1e3, 3)
+            r["jacobi_sweep_us"] = round(st.region_ns / max(1, st.regions) / 1e3, 2)
+            r["jacobi_region_rpcs"] = int(st.rpc_calls[gf.OP_REGION])
+    p, q = res["persistent"], res["split"]
+    line = {"metric": "region cost: persistent grid vs kernel split", "value": q["region_64B_us"]["p50"],
+            "unit": "us per 64-byte region (kernel split)", "n_gpus": 1, "higher_is_better": False,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "64-byte region x 400; axpy_sum N = 2^20; 256 loops one region each; "
+                                   "Jacobi 256^3 x 100 sweeps (no final write)"},
+            "detail": {**res,
+                       "split_over_persistent": {"region_64B": round(q["region_64B_us"]["p50"] /
+                                                                     p["region_64B_us"]["p50"], 2),
+                                                 "axpy_sum": round(q["axpy_sum_2^20_ms"] / p["axpy_sum_2^20_ms"], 2),
+                                                 "loops_256": round(q["loops_256_regions"]["program_ms"] /
+                                                                    p["loops_256_regions"]["program_ms"], 2),
+                                                 "jacobi": round(q["jacobi_256x100_ms"] / p["jacobi_256x100_ms"], 3)}}}
+    print(json.dumps(line))
+    shutil.rmtree(tmp, ignore_errors=True)
+
+
 def run(args):
     {"stress": stress, "batch": batch, "learned": learned, "serve": serve_run, "e1": e1,
-     "link": link, "hbm": hbm}[args.workload](args)
+     "link": link, "hbm": hbm, "split": split}[args.workload](args)

@@ -48,6 +48,12 @@ def test_strerror_and_defaults_without_gpu(lib):
     bad.ring_slots = 1000                                   # not a power of two
     h = ctypes.c_void_p()
     assert gf.gf_init(ctypes.byref(bad), ctypes.byref(h)) == gf.GF_EINVAL
+    assert c.split_regions == 0                             # regions on the persistent grid by default
+    for split, threads in ((1, 0), (2, 1)):                 # the split needs a server thread; 0/1 only
+        bad = gf.gf_config()
+        gf.gf_config_default(ctypes.byref(bad))
+        bad.split_regions, bad.server_threads = split, threads
+        assert gf.gf_init(ctypes.byref(bad), ctypes.byref(h)) == gf.GF_EINVAL
 
 
 def test_programs_registered(lib):
