@@ -130,20 +130,40 @@ class Clocks:
                 "reasons": reasons, "samples": len(sm)}
 
 
-def cpu_oracle_sample(n, sweeps, tmp):
-    """Times the serial C oracle (1 thread) on `sweeps` sweeps of the same grid."""
-    import numpy as np
+def host_cores():
+    """Cores this process may run on (the GPU machine's host share)."""
+    try:
+        return sorted(os.sched_getaffinity(0))
+    except AttributeError:
+        return list(range(os.cpu_count() or 1))
+
+
+def cpu_oracle_sample(n, sweeps, tmp, omp=False, reps=3):
+    """Times the serial C oracle on `sweeps` sweeps of the same grid: pinned to
+    one core, best of `reps`.  omp=True times the same C built with OpenMP on
+    every available core instead (a CPU baseline like the paper's; timing
+    only).  Returns (GB/s, seconds, cores)."""
     from oracle import build as ob
     from paper_2306_11686_gb300 import inputs
     ob.build()
     path = os.path.join(tmp, "in.bin")
     if not os.path.exists(path):
         inputs.write_f64(path, inputs.jacobi_input(n, seed=2))
-    t0 = time.perf_counter()
-    subprocess.run([ob.binary("jacobi"), str(n), str(sweeps), path, os.path.join(tmp, "ref.bin")],
-                   check=True, stdout=subprocess.DEVNULL)
-    dt = time.perf_counter() - t0
-    return loop_bytes(n, sweeps) / dt / 1e9, dt
+    cores = host_cores()
+    env = dict(os.environ)
+    if omp:
+        env["OMP_NUM_THREADS"] = str(len(cores))
+        env["OMP_PROC_BIND"] = "close"
+    # pinning by a taskset prefix, not preexec_fn: this process has live threads
+    pin = ["taskset", "-c", str(cores[0])] if not omp and shutil.which("taskset") else []
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        subprocess.run(pin + [ob.binary("jacobi_omp" if omp else "jacobi"), str(n), str(sweeps), path,
+                              os.path.join(tmp, "ref.bin")], check=True, stdout=subprocess.DEVNULL, env=env)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return loop_bytes(n, sweeps) / best / 1e9, best, (len(cores) if omp else 1), bool(pin) or omp
 
 
 def run_reference(args):
@@ -153,10 +173,10 @@ def run_reference(args):
     tmp = tempfile.mkdtemp(prefix="gfbench", dir=args.out_dir or default_out_dir())
     sample = max(1, args.ref_sweeps)
     for _ in range(args.warmup):
-        cpu_oracle_sample(N, sample, tmp)
+        cpu_oracle_sample(N, sample, tmp, reps=1)
     vals, times = [], []
     for _ in range(args.steps):
-        v, dt = cpu_oracle_sample(N, sample, tmp)
+        v, dt, _, _ = cpu_oracle_sample(N, sample, tmp, reps=1)
         vals.append(v)
         times.append(dt)
     v = sum(loop_bytes(N, sample) for _ in times) / sum(times) / 1e9
@@ -185,6 +205,8 @@ def main():
                     help="where the program writes its final grid (default: /dev/shm when it is a writable "
                          "tmpfs, so the number measures the runtime and the page cache, not the disk)")
     ap.add_argument("--sweeps", type=int, default=SWEEPS, help="sweeps per program (100 = the benchmark workload)")
+    ap.add_argument("--hbm-log2", type=int, default=None,
+                    help="--workload hbm: one loop of 2^k iterations only (default: 2^26 and 2^28)")
     ap.add_argument("--int-adds", type=int, default=None,
                     help="how many of the five neighbour adds run on the integer pipe (0..5; the program's "
                          "default when omitted)")
@@ -295,11 +317,16 @@ def main():
         pass
     fp64_peak = sms * 2 * sm_mhz * 1e6                               # FP64 operations / s
     fp64_ops = FP64_OPS_PER_POINT * (N - 2) ** 3 * sweeps
-    cpu = None
+    cpu = cpu_omp = None
     if rank == 0 and args.cpu_sweeps > 0:
-        cv, cdt = cpu_oracle_sample(N, args.cpu_sweeps, tmp)
-        cpu = {"value": round(cv, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_sweeps} sweeps of the {N}^3 grid ({cdt:.2f} s)"}
+        cv, cdt, cc, pinned = cpu_oracle_sample(N, args.cpu_sweeps, tmp)
+        cpu = {"value": round(cv, 3), "unit": "GB/s", "cores": cc, "kind": "oracle",
+               "sample": f"{args.cpu_sweeps} sweeps of the {N}^3 grid, "
+                         f"{'pinned to one core' if pinned else 'one thread (not pinned)'}, best of 3 "
+                         f"({cdt:.2f} s); host cores available: {len(host_cores())}"}
+        ov, odt, oc, _ = cpu_oracle_sample(N, args.cpu_sweeps, tmp, omp=True)
+        cpu_omp = {"value": round(ov, 3), "unit": "GB/s", "cores": oc, "kind": "oracle source built with OpenMP",
+                   "sample": f"{args.cpu_sweeps} sweeps of the {N}^3 grid on {oc} threads, best of 3 ({odt:.3f} s)"}
     if rank == 0:
         line = {
             "metric": "loop GB/s (% HBM peak)", "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
@@ -330,6 +357,7 @@ def main():
                     "d2h_bytes_per_step": N ** 3 * 8 + 100 * 24},
             "gpu_launches": args.steps,
             "cpu_baseline": cpu,
+            "cpu_openmp": cpu_omp,
             "clocks": clk.summary(),
             "detail": {"main_ns": st.main_ns, "regions": st.regions, "region_ns": st.region_ns,
                        "sweep_us": round(st.region_ns / max(1, st.regions) / 1e3, 2),

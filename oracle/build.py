@@ -12,7 +12,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "_build")
 SOURCES = ["axpy_sum", "jacobi", "exact_sum", "stress", "spmv_serve", "loops", "synth"]
-CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-Wall"]
+CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-Wall", "-Wno-unknown-pragmas"]
 
 
 def binary(name: str) -> str:
@@ -31,6 +31,13 @@ def build(force: bool = False) -> None:
             continue
         procs.append((name, subprocess.Popen(["gcc", *CFLAGS, "-o", out, src, "-lm"],
                                              stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    # the same Jacobi source built with OpenMP: a timed all-core CPU baseline
+    # (bench.py), never a parity reference
+    src = os.path.join(HERE, "jacobi.c")
+    out = binary("jacobi_omp")
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        procs.append(("jacobi_omp", subprocess.Popen(["gcc", *CFLAGS, "-fopenmp", "-o", out, src, "-lm"],
+                                                     stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     for name, p in procs:
         out, _ = p.communicate()
         if p.returncode != 0:

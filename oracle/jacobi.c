@@ -46,6 +46,10 @@ int main(int argc, char **argv)
             return 4;
         }
         double res = 0.0;
+        /* ignored by the plain build (the oracle); the -fopenmp build of this
+         * same file is only a timed all-core CPU baseline, never a parity
+         * reference: max is order-independent, so its output is the same */
+#pragma omp parallel for collapse(2) reduction(max : res)
         for (long k = 0; k < n; k++)
             for (long j = 0; j < n; j++)
                 for (long i = 0; i < n; i++) {

@@ -245,7 +245,7 @@ def hbm(args):
         pass
     res = {}
     stream = torch.cuda.Stream()
-    for lg in (26, 28):
+    for lg in ((args.hbm_log2,) if getattr(args, "hbm_log2", None) else (26, 28)):
         n = 1 << lg
         x = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1, 1)
         y = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1, 1)

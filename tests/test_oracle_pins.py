@@ -274,3 +274,18 @@ def test_spmv_serve_oracle_hand_case(oracle_bin, tmp_path, monkeypatch):
     assert rec[16:] == (_mix(key) & MASK).to_bytes(8, "little")[:5]
     res = np.fromfile(tmp_path / "res.bin", dtype=np.int64)
     assert res[0] == 21 and res[1] == len(out) and res[2] == -1 and res[3] == 3
+
+
+def test_jacobi_openmp_build_prints_and_writes_the_same(oracle_bin, tmp_path):
+    """The all-core CPU baseline (the Jacobi oracle's source built with
+    OpenMP) computes exactly what the serial oracle does."""
+    import os
+    from paper_2306_11686_gb300 import inputs
+    g = inputs.jacobi_input(40, seed=5)
+    inputs.write_f64(tmp_path / "in.bin", g)
+    a = subprocess.run([oracle_bin("jacobi"), "40", "6", tmp_path / "in.bin", tmp_path / "a.bin"],
+                       capture_output=True, text=True, check=True).stdout
+    b = subprocess.run([oracle_bin("jacobi_omp"), "40", "6", tmp_path / "in.bin", tmp_path / "b.bin"],
+                       capture_output=True, text=True, check=True, env={**os.environ, "OMP_NUM_THREADS": "4"}).stdout
+    assert a == b
+    assert (tmp_path / "a.bin").read_bytes() == (tmp_path / "b.bin").read_bytes()
