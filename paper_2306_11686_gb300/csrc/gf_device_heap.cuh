@@ -17,7 +17,9 @@
  *  - every lane pops and pushes its own block on the stack of its lane index,
  *    so a warp's 32 requests are 32 independent CASes issued together: no
  *    list is walked (a single stack per (SM, class) would need a warp's leader
- *    to follow 32 dependent next-links, about 16 us, before its one CAS);
+ *    to follow 32 dependent next-links, about 16 us, before its one CAS); the
+ *    first attempts run a fixed number of times with no early exit, so the
+ *    lanes stay together through contention;
  *  - lanes whose stack is empty are served together by one bump of the
  *    current slab (the leader of the lanes that ask for the same class,
  *    __match_any_sync); with no fresh slab left they take blocks from the
@@ -60,41 +62,58 @@ __device__ __forceinline__ unsigned long long *stack_of(gf_heap *H, uint32_t sm,
     return &heads(H)[((size_t)sm * GF_HEAP_NCLASS + cls) * GF_HEAP_LANES + sub];
 }
 
-/* pop one block from stack (sm, cls, sub); 0 if it is empty (or stays contended) */
+/* pop: three attempts with a fixed trip count (no early exit), so the lanes of
+ * a warp leave together; 0 if empty or still contended */
 static __device__ __forceinline__ uint64_t heap_pop1(gf_heap *H, uint32_t sm, uint32_t cls, uint32_t sub)
 {
     unsigned long long *head = stack_of(H, sm, cls, sub);
     const uint32_t max1 = (uint32_t)(H->slab_bytes >> 4);
-    for (int attempt = 0; attempt < 64; attempt++) {
-        const unsigned long long h = *(volatile unsigned long long *)head;
-        const uint32_t cur = (uint32_t)h;
-        if (cur == 0)
-            return 0;
-        const uint32_t nxt = *(volatile uint32_t *)node_addr(H, cur);
-        if (nxt > max1)                /* block reused under us: the CAS would fail */
-            continue;
-        if (atomicCAS(head, h, ((h >> 32) + 1ull) << 32 | nxt) == h) {
-            __threadfence();
-            return node_addr(H, cur);
+    uint64_t got = 0;
+    bool stop = false;
+#pragma unroll
+    for (int attempt = 0; attempt < 3; attempt++) {
+        if (!stop) {
+            const unsigned long long h = *(volatile unsigned long long *)head;
+            const uint32_t cur = (uint32_t)h;
+            if (cur == 0) {
+                stop = true;
+            } else {
+                const uint32_t nxt = *(volatile uint32_t *)node_addr(H, cur);
+                if (nxt <= max1 && atomicCAS(head, h, ((h >> 32) + 1ull) << 32 | nxt) == h) {
+                    got = node_addr(H, cur);
+                    stop = true;
+                }
+            }
         }
     }
-    return 0;
+    if (got)
+        __threadfence();
+    return got;
 }
 
-/* push block a (node index node) onto stack (sm, cls, sub); false after a
- * contention bound no sane run reaches */
+/* push: three attempts with a fixed trip count, then (rarely) a retry loop;
+ * false after a contention bound no sane run reaches */
 static __device__ __forceinline__ bool heap_push1(gf_heap *H, uint32_t sm, uint32_t cls, uint32_t sub, uint64_t a,
                                                    uint32_t node)
 {
     unsigned long long *head = stack_of(H, sm, cls, sub);
-    for (int attempt = 0; attempt < (1 << 20); attempt++) {
+    bool done = false;
+#pragma unroll
+    for (int attempt = 0; attempt < 3; attempt++) {
+        if (!done) {
+            const unsigned long long h = *(volatile unsigned long long *)head;
+            *(volatile uint32_t *)a = (uint32_t)h;
+            __threadfence();
+            done = atomicCAS(head, h, ((h >> 32) + 1ull) << 32 | node) == h;
+        }
+    }
+    for (int attempt = 0; attempt < (1 << 20) && !done; attempt++) {
         const unsigned long long h = *(volatile unsigned long long *)head;
         *(volatile uint32_t *)a = (uint32_t)h;
         __threadfence();
-        if (atomicCAS(head, h, ((h >> 32) + 1ull) << 32 | node) == h)
-            return true;
+        done = atomicCAS(head, h, ((h >> 32) + 1ull) << 32 | node) == h;
     }
-    return false;
+    return done;
 }
 
 /* a block of (cls) from any stack other than (sm, cls, own): the rest of this

@@ -3,7 +3,8 @@
 Pipeline (the learned-model pattern on top of the runtime):
   1. `measure`: the autotuner times every candidate shape of every loop
      natively (gf_synth_time: CUDA events, fastest of `reps` runs after a
-     warm-up); its per-loop optimum is the judge of regret.
+     warm-up); its per-loop optimum is the reference regret is measured
+     against.
   2. `train`: an FP32 MLP (3 hidden layers of 64 ReLU units) learns log(ms)
      from gf_tune_features(loop, shape) on the training loops (torch).
   3. `evaluate`: on held-out loops the model's choice (gf_mlp_choose, the C++
@@ -179,7 +180,7 @@ def evaluate(params, loops, shs, ms, sms, refine_k=3, ctx=None, x=None, z=None, 
              upwards: that minimum is the luckiest of 96 noisy timings);
     retimed: the model's choices, the autotuner's choice and the plain shape
              re-timed side by side (`reps` runs each), regret against the
-             autotuner's choice -- the judge.  Needs ctx, x, z."""
+             autotuner's choice -- the fair comparison.  Needs ctx, x, z."""
     h = shs.index(heuristic_shape(sms))
     res = {"n": len(loops), "refine_k": refine_k}
     t1, tr, th = [], [], []
