@@ -96,6 +96,9 @@ typedef struct gf_buf {
 /* Counters of the last program waited for on this context (host fields
  * accumulate over the context's life). */
 #define GF_NOPS 16
+/* Built-in opcodes, the index of rpc_calls / rpc_slots: 1 printf / fprintf,
+ * 2 fopen, 3 fwrite, 4 fclose, 5 clock, 6 getenv, 7 fread, 8 fflush,
+ * 9 strtod (the device's slow path), 10 region launch (kernel split only). */
 typedef struct gf_stats {
     uint64_t rpc_calls[GF_NOPS];  /* lane records per opcode (index = GF_OP_*)               */
     uint64_t rpc_slots[GF_NOPS];  /* ring slots per opcode (calls / slots = aggregation)    */
