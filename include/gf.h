@@ -117,6 +117,10 @@ typedef struct gf_stats {
     int32_t grid, block;          /* launch shape of the last program                      */
     int32_t error;                /* first device-side error of the last program           */
     int32_t exit_code;
+    uint64_t heap_ns;             /* the initial thread's time inside malloc / free        */
+    uint64_t copy_regions;        /* regions that moved large fwrite/fread data through the
+                                     bulk arena (included in regions)                      */
+    uint64_t copy_ns;             /* their device time (included in region_ns)             */
 } gf_stats;
 
 /* Host landing pad for a user opcode (>= 256).  `rec` points at the lane

@@ -317,7 +317,7 @@ static __device__ bool large_free(gf_heap *H, uint64_t addr, int64_t timeout_ns)
 } // namespace gfd
 
 /* ====================================================================== malloc / free */
-static __device__ __noinline__ void *gf_malloc(size_t n)
+static __device__ __forceinline__ void *gf_malloc_body(size_t n)
 {
     gf_state *S = gfd::s_st;
     gf_heap *H = &S->heap;
@@ -375,7 +375,7 @@ static __device__ __noinline__ void *gf_malloc(size_t n)
     return (void *)p;
 }
 
-static __device__ __noinline__ void gf_free(void *p)
+static __device__ __forceinline__ void gf_free_body(void *p)
 {
     if (!p)
         return;
@@ -423,6 +423,27 @@ static __device__ __noinline__ void gf_free(void *p)
         atomicAdd((unsigned long long *)&H->live_bytes, 0ull - bs * nd);
     }
     __syncwarp(grp);                   /* leave together, as in gf_malloc */
+}
+
+/* malloc / free; the initial thread's time in them is counted (st_heap_ns),
+ * so a program's serial heap cost shows apart from its regions and RPCs */
+static __device__ __noinline__ void *gf_malloc(size_t n)
+{
+    const bool timed = gfd::is_initial_thread();
+    const uint64_t t0 = timed ? gfd::now_ns() : 0;
+    void *p = gf_malloc_body(n);
+    if (timed)
+        gfd::s_st->st_heap_ns += gfd::now_ns() - t0;
+    return p;
+}
+
+static __device__ __noinline__ void gf_free(void *p)
+{
+    const bool timed = gfd::is_initial_thread();
+    const uint64_t t0 = timed ? gfd::now_ns() : 0;
+    gf_free_body(p);
+    if (timed)
+        gfd::s_st->st_heap_ns += gfd::now_ns() - t0;
 }
 
 /* size of the heap block holding p (0 if p is not a live heap block start) */

@@ -429,7 +429,19 @@ static __device__ __noinline__ int64_t rpc_finish1(unsigned long long t, int *st
 
 /* dst[0 .. bytes) = src[...] by the whole grid: 16-byte vector copies when
  * both ends are 16-byte aligned, bytewise otherwise.  Initial thread only. */
+static __device__ int copy_region_body(void *dst, const void *src, uint64_t bytes);
+
+/* a grid-wide copy (initial thread), timed apart from the program's own regions */
 static __device__ __noinline__ int copy_region(void *dst, const void *src, uint64_t bytes)
+{
+    const uint64_t t0 = now_ns();
+    const int rc = copy_region_body(dst, src, bytes);
+    s_st->st_copy_regions++;
+    s_st->st_copy_ns += now_ns() - t0;
+    return rc;
+}
+
+static __device__ int copy_region_body(void *dst, const void *src, uint64_t bytes)
 {
     if ((((uintptr_t)dst | (uintptr_t)src) & 15u) == 0) {
         const uint64_t n16 = bytes >> 4;

@@ -180,6 +180,9 @@ typedef struct gf_state {
     uint64_t st_wait_ns;          /* device ns spent waiting for the host             */
     uint64_t st_regions;
     uint64_t st_region_ns;        /* initial thread: publish -> all blocks done       */
+    uint64_t st_heap_ns;          /* initial thread: time inside gf_malloc / gf_free   */
+    uint64_t st_copy_regions;     /* regions that copied through the bulk arena        */
+    uint64_t st_copy_ns;          /* their time (also counted in st_region_ns)         */
     uint64_t t_main_start, t_main_end;
     uint64_t lat_hist[GF_LAT_BUCKETS];  /* RPC round trips (claim -> host done), lane records */
     uint32_t rand_words[40];      /* rand() state of the program (device libc)        */

@@ -38,7 +38,7 @@
 #define GF_MAX_BLOCKS_PER_SM 32
 #define GF_ARGV_BYTES (64u * 1024u)
 #define GF_DMA_CHUNK (16ull << 20)
-#define GF_DMA_NSTAGE 8            /* pinned staging buffers of GF_DMA_CHUNK bytes */
+#define GF_DMA_LANES 4             /* independent copy-engine lanes (one per server thread, up to 4) */
 #define GF_INTERN_BYTES (1u << 20)
 #define GF_BLOCK_THREADS 256
 
@@ -76,6 +76,18 @@ struct Staged {
     uint32_t dir;
     bool owned;
 };
+
+/* One copy-engine lane: two pinned staging buffers of GF_DMA_CHUNK bytes
+ * (double buffering), a stream and its events.  Server thread t uses lane
+ * t % GF_DMA_LANES, so the threads' DMAs run side by side instead of
+ * queueing behind one context-wide lock. */
+struct DmaLane {
+    std::mutex mu;
+    cudaStream_t stream = nullptr;
+    void *stage[2] = {};
+    cudaEvent_t ev[2] = {};
+};
+static thread_local int tl_dma_lane = 0;
 
 struct Instance {
     int idx = 0;
@@ -124,10 +136,8 @@ struct gf_ctx {
     std::atomic<int> nactive{0};
     std::mutex act_mu;
     std::condition_variable act_cv;
-    cudaStream_t own_stream = nullptr, dma_stream = nullptr;
-    void *dma_stage[GF_DMA_NSTAGE] = {};
-    cudaEvent_t dma_ev[GF_DMA_NSTAGE] = {};
-    std::mutex dma_mu;
+    cudaStream_t own_stream = nullptr;
+    DmaLane dma[GF_DMA_LANES];
     uint8_t *intern_host = nullptr;
     uint64_t intern_dev = 0;
     size_t intern_used = 0;
@@ -195,92 +205,67 @@ static bool pow2(uint64_t x) { return x && !(x & (x - 1)); }
 
 /* ------------------------------------------------------------------ DMA */
 /*
- * Device -> host streaming through the pinned staging buffers.  Chunk k goes
- * to buffer k % nbuf; a buffer is refilled only after the sink has consumed
- * its previous chunk.  Sequential mode double-buffers one copy against one
- * sink call; parallel mode hands each landed chunk to its own writer thread
- * so up to GF_DMA_NSTAGE sink calls run at once.
+ * Device -> host streaming through the calling server thread's lane: chunk k
+ * goes to staging buffer k % 2, and the copy of chunk k overlaps the sink's
+ * work on chunk k - 1; chunks reach the sink in order.  Returns the length of
+ * the prefix the sink accepted.
  */
 static uint64_t dma_d2h(gf_ctx *c, uint64_t dev, uint64_t bytes, const gfh::sink_fn &sink, bool parallel)
 {
-    std::lock_guard<std::mutex> g(c->dma_mu);
-    const int nbuf = parallel ? GF_DMA_NSTAGE : 2;
+    (void)parallel;                       /* chunks are always handed over in order */
+    DmaLane &L = c->dma[tl_dma_lane % GF_DMA_LANES];
+    std::lock_guard<std::mutex> g(L.mu);
     const uint64_t nchunk = (bytes + GF_DMA_CHUNK - 1) / GF_DMA_CHUNK;
-    std::vector<std::thread> writer(nbuf);
-    std::vector<int> ok(nchunk, 0);
-    std::vector<uint64_t> pend(nbuf, UINT64_MAX);   /* chunk held by each buffer in sequential mode */
+    uint64_t pend[2] = {UINT64_MAX, UINT64_MAX};   /* chunk held by each staging buffer */
+    uint64_t delivered = 0;
     bool failed = false;
-    auto consume_seq = [&](int k) {
+    auto consume = [&](int k) {
         if (pend[k] == UINT64_MAX)
             return;
         const uint64_t ch = pend[k], off = ch * GF_DMA_CHUNK, n = std::min<uint64_t>(GF_DMA_CHUNK, bytes - off);
-        ok[ch] = !failed && cudaEventSynchronize(c->dma_ev[k]) == cudaSuccess && sink(c->dma_stage[k], n, off);
-        failed |= !ok[ch];
+        if (!failed && cudaEventSynchronize(L.ev[k]) == cudaSuccess && sink(L.stage[k], n, off))
+            delivered += n;
+        else
+            failed = true;
         pend[k] = UINT64_MAX;
     };
     for (uint64_t ch = 0; ch < nchunk && !failed; ch++) {
-        const int k = (int)(ch % nbuf);
+        const int k = (int)(ch & 1);
+        consume(k);                       /* the buffer's previous chunk goes out first */
         const uint64_t off = ch * GF_DMA_CHUNK, n = std::min<uint64_t>(GF_DMA_CHUNK, bytes - off);
-        if (parallel) {
-            if (writer[k].joinable())
-                writer[k].join();
-        } else {
-            consume_seq(k);
-        }
-        if (cudaMemcpyAsync(c->dma_stage[k], (const void *)(dev + off), n, cudaMemcpyDeviceToHost, c->dma_stream) !=
+        if (cudaMemcpyAsync(L.stage[k], (const void *)(dev + off), n, cudaMemcpyDeviceToHost, L.stream) !=
                 cudaSuccess ||
-            cudaEventRecord(c->dma_ev[k], c->dma_stream) != cudaSuccess) {
+            cudaEventRecord(L.ev[k], L.stream) != cudaSuccess) {
             failed = true;
             break;
         }
-        if (parallel) {
-            writer[k] = std::thread([&, k, ch, off, n] {
-                ok[ch] = cudaEventSynchronize(c->dma_ev[k]) == cudaSuccess && sink(c->dma_stage[k], n, off);
-            });
-        } else {
-            pend[k] = ch;
-            consume_seq(1 - k);   /* the other buffer's chunk landed while this copy was issued */
-        }
+        pend[k] = ch;
+        consume(1 - k);                   /* the other buffer's chunk landed while this copy was issued */
     }
-    if (parallel) {
-        for (auto &t : writer)
-            if (t.joinable())
-                t.join();
-    } else {
-        /* drain in chunk order */
-        for (int round = 0; round < 2; round++) {
-            int best = -1;
-            for (int k = 0; k < nbuf; k++)
-                if (pend[k] != UINT64_MAX && (best < 0 || pend[k] < pend[best]))
-                    best = k;
-            if (best >= 0)
-                consume_seq(best);
-        }
-    }
-    cudaStreamSynchronize(c->dma_stream);
-    uint64_t delivered = 0;
-    for (uint64_t ch = 0; ch < nchunk && ok[ch]; ch++)
-        delivered += std::min<uint64_t>(GF_DMA_CHUNK, bytes - ch * GF_DMA_CHUNK);
+    consume(nchunk & 1 ? 0 : 1);          /* drain in chunk order: the older pending chunk first */
+    consume(nchunk & 1 ? 1 : 0);
+    cudaStreamSynchronize(L.stream);
     return delivered;
 }
 
 static uint64_t dma_h2d(gf_ctx *c, uint64_t dev, uint64_t bytes, const gfh::source_fn &src)
 {
-    std::lock_guard<std::mutex> g(c->dma_mu);
+    DmaLane &L = c->dma[tl_dma_lane % GF_DMA_LANES];
+    std::lock_guard<std::mutex> g(L.mu);
     uint64_t off = 0;
     int b = 0;
     bool inflight[2] = {false, false};
     while (off < bytes) {
         if (inflight[b]) {
-            cudaEventSynchronize(c->dma_ev[b]);
+            cudaEventSynchronize(L.ev[b]);
             inflight[b] = false;
         }
         const uint64_t want = std::min<uint64_t>(GF_DMA_CHUNK, bytes - off);
-        const uint64_t got = src(c->dma_stage[b], want);
+        const uint64_t got = src(L.stage[b], want);
         if (got) {
-            if (cudaMemcpyAsync((void *)(dev + off), c->dma_stage[b], got, cudaMemcpyHostToDevice, c->dma_stream) !=
+            if (cudaMemcpyAsync((void *)(dev + off), L.stage[b], got, cudaMemcpyHostToDevice, L.stream) !=
                     cudaSuccess ||
-                cudaEventRecord(c->dma_ev[b], c->dma_stream) != cudaSuccess)
+                cudaEventRecord(L.ev[b], L.stream) != cudaSuccess)
                 break;
             inflight[b] = true;
             off += got;
@@ -289,13 +274,14 @@ static uint64_t dma_h2d(gf_ctx *c, uint64_t dev, uint64_t bytes, const gfh::sour
             break;
         b = 1 - b;
     }
-    cudaStreamSynchronize(c->dma_stream);
+    cudaStreamSynchronize(L.stream);
     return off;
 }
 
 /* ------------------------------------------------------------------ server threads */
 static void server_main(gf_ctx *c, uint32_t tid, uint32_t nthr)
 {
+    tl_dma_lane = (int)(tid % GF_DMA_LANES);
     uint32_t idle = 0;
     while (!c->stop.load(std::memory_order_relaxed)) {
         int n = 0;
@@ -399,14 +385,16 @@ extern "C" GF_API int gf_finalize(gf_ctx *c)
         cudaFreeHost(c->ring_host);
     if (c->intern_host)
         cudaFreeHost(c->intern_host);
-    for (int k = 0; k < GF_DMA_NSTAGE; k++) {
-        if (c->dma_stage[k])
-            cudaFreeHost(c->dma_stage[k]);
-        if (c->dma_ev[k])
-            cudaEventDestroy(c->dma_ev[k]);
+    for (DmaLane &L : c->dma) {
+        for (int k = 0; k < 2; k++) {
+            if (L.stage[k])
+                cudaFreeHost(L.stage[k]);
+            if (L.ev[k])
+                cudaEventDestroy(L.ev[k]);
+        }
+        if (L.stream)
+            cudaStreamDestroy(L.stream);
     }
-    if (c->dma_stream)
-        cudaStreamDestroy(c->dma_stream);
     if (c->own_stream)
         cudaStreamDestroy(c->own_stream);
     delete c;
@@ -466,14 +454,17 @@ extern "C" GF_API int gf_init(const gf_config *cfg, gf_ctx **out)
     void *idv = nullptr;
     cudaHostGetDevicePointer(&idv, c->intern_host, 0);
     c->intern_dev = (uint64_t)idv;
-    for (int k = 0; k < GF_DMA_NSTAGE; k++) {
-        if (cudaHostAlloc(&c->dma_stage[k], GF_DMA_CHUNK, cudaHostAllocPortable) != cudaSuccess)
-            return fail(GF_ENOMEM);
-        if (cudaEventCreateWithFlags(&c->dma_ev[k], cudaEventDisableTiming) != cudaSuccess)
+    for (DmaLane &L : c->dma) {
+        for (int k = 0; k < 2; k++) {
+            if (cudaHostAlloc(&L.stage[k], GF_DMA_CHUNK, cudaHostAllocPortable) != cudaSuccess)
+                return fail(GF_ENOMEM);
+            if (cudaEventCreateWithFlags(&L.ev[k], cudaEventDisableTiming) != cudaSuccess)
+                return fail(GF_ECUDA);
+        }
+        if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess)
             return fail(GF_ECUDA);
     }
-    if (cudaStreamCreateWithFlags(&c->dma_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
         return fail(GF_ECUDA);
     for (uint32_t k = 0; k < cf.max_programs; k++) {
         Instance *in = new Instance();
@@ -891,6 +882,9 @@ extern "C" GF_API int gf_wait(gf_handle *h, int *exit_code, int64_t timeout_ns)
         st.block = (int32_t)h->block;
         st.error = f.error;
         st.exit_code = f.exit_code;
+        st.heap_ns = f.st_heap_ns;
+        st.copy_regions = f.st_copy_regions;
+        st.copy_ns = f.st_copy_ns;
     }
     if (rc == GF_OK && in->h_final.error)
         rc = in->h_final.error;

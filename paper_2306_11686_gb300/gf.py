@@ -74,6 +74,9 @@ class gf_stats(ctypes.Structure):
         ("block", ctypes.c_int32),
         ("error", ctypes.c_int32),
         ("exit_code", ctypes.c_int32),
+        ("heap_ns", ctypes.c_uint64),
+        ("copy_regions", ctypes.c_uint64),
+        ("copy_ns", ctypes.c_uint64),
     ]
 
     def as_dict(self):
