@@ -45,6 +45,14 @@ GF_MAIN_BOUNDS(spmv_serve, 4)(int argc, char **argv)
     GF_FILE f = gf_fopen(argv[4], "wb");
     if (!f)
         return 3;
+    /* one bit per row: set for the rows that issue a request in this pass, so
+     * a row without one skips the request search with a single load */
+    const long long nw = (n + 31) / 32;
+    unsigned *mark = (unsigned *)gf_malloc((size_t)(nw > 0 ? nw : 1) * 4);
+    if (!mark)
+        return 4;
+    if (gf_parallel_for(0, nw, GF_SCHED_STATIC, 1, [=](int64_t w) { mark[w] = 0u; }))
+        return 10;
     double *x = xb, *y = yb;
     long long q0 = 0;
     for (int r = 0; r < R; r++) {
@@ -55,6 +63,11 @@ GF_MAIN_BOUNDS(spmv_serve, 4)(int argc, char **argv)
         const int rr = r;
         const double *xs = x;
         double *ys = y;
+        if (qb > qa && gf_parallel_for(qa, qb, GF_SCHED_STATIC, 1, [=](int64_t q) {
+                const unsigned row = (unsigned)(req[2 * q] & 0xffffffffll);
+                atomicOr(&mark[row >> 5], 1u << (row & 31));
+            }))
+            return 10;
         const int rc = gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) {
             double s = 0.0;
             /* unrolled: the loads of eight nonzeros are in flight together (the
@@ -63,7 +76,7 @@ GF_MAIN_BOUNDS(spmv_serve, 4)(int argc, char **argv)
             for (long long j = rowptr[i]; j < rowptr[i + 1]; j++)
                 s = s + val[j] * xs[col[j]];
             ys[i] = s;
-            if (qa == qb)
+            if (qa == qb || !((mark[i >> 5] >> (i & 31)) & 1u))
                 return;
             const long long key = ((long long)rr << 32) | (long long)i;
             long long lo = qa, hi = qb;                 /* first request with key >= (pass, row) */
@@ -105,6 +118,10 @@ GF_MAIN_BOUNDS(spmv_serve, 4)(int argc, char **argv)
         });
         if (rc)
             return 10;
+        if (qb > qa && gf_parallel_for(qa, qb, GF_SCHED_STATIC, 1, [=](int64_t q) {
+                mark[(unsigned)(req[2 * q] & 0xffffffffll) >> 5] = 0u;   /* clear for the next pass */
+            }))
+            return 10;
         q0 = q1;
         double *t = x;
         x = y;
@@ -116,5 +133,6 @@ GF_MAIN_BOUNDS(spmv_serve, 4)(int argc, char **argv)
             return 10;
     }
     gf_fclose(f);
+    gf_free(mark);
     return 0;
 }

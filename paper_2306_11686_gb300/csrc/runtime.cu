@@ -37,8 +37,8 @@
 
 #define GF_MAX_BLOCKS_PER_SM 32
 #define GF_ARGV_BYTES (64u * 1024u)
-#define GF_DMA_CHUNK (16ull << 20)
-#define GF_DMA_LANES 4             /* independent copy-engine lanes (one per server thread, up to 4) */
+#define GF_DMA_CHUNK (8ull << 20)
+#define GF_DMA_LANES 8             /* independent copy-engine lanes (one per server thread, up to 8) */
 #define GF_INTERN_BYTES (1u << 20)
 #define GF_BLOCK_THREADS 256
 

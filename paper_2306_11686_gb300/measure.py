@@ -138,6 +138,9 @@ def learned(args):
     print(json.dumps(line))
 
 
+SERVE_THREADS = 4
+
+
 def serve_run(args):
     from . import serve
     P, n = 64, 1 << 20
@@ -149,10 +152,18 @@ def serve_run(args):
     progs = [serve.Program(p, n, 10, 64) for p in range(P)]
     t_gen = time.time() - t0
     outs = [os.path.join(tmp, f"rec{p}.bin") for p in range(P)]
-    recs, agg = serve.serve(progs, outs, max_concurrent=16, rate_hz=400.0, heap_bytes=1 << 30, ring_slots=1024,
-                            server_threads=4, stdout_path=os.path.join(tmp, "out.txt"))
+    runs = []
+    for _ in range(3):                  # the median of three runs (a run varies by about 10%)
+        recs, agg = serve.serve(progs, outs, max_concurrent=16, rate_hz=400.0, heap_bytes=1 << 30, ring_slots=1024,
+                                server_threads=SERVE_THREADS, stdout_path=os.path.join(tmp, "out.txt"))
+        agg["errors"] = sum(1 for r in recs if r["rc"] or r["exit"])
+        runs.append(agg)
+    runs.sort(key=lambda a: a["calls_per_s"])
+    agg = dict(runs[1])
+    agg["calls_per_s_runs"] = [round(a["calls_per_s"]) for a in runs]
+    agg["errors"] = sum(a["errors"] for a in runs)
+    agg["server_threads"] = SERVE_THREADS
     agg["input_gen_s"] = t_gen
-    agg["errors"] = sum(1 for r in recs if r["rc"] or r["exit"])
     line = {"metric": "RPC calls/s + p99 latency", "value": round(agg["calls_per_s"]), "unit": "calls/s",
             "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "64 programs, CSR SpMV 1M rows x 16 nnz, 10 passes, Poisson libc requests, "
