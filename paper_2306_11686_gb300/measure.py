@@ -291,7 +291,7 @@ def hbm(args):
     best = max(v["GBps"] for v in res.values())
     line = {"metric": "loop GB/s (% HBM peak)", "value": round(best, 1), "unit": "GB/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "one axpy loop z = 2.5 x + y, N = 2^26 and 2^28, static chunk 1, "
+            "config": {"workload": "one axpy loop z = 2.5 x + y, N = " + " and ".join(res) + ", static chunk 1, "
                                    "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": round(best, 1), "peak": peak, "unit": "GB/s",
                          "frac": None if not peak else round(best / peak, 4), "peak_kind": "measured"},
