@@ -207,6 +207,8 @@ def main():
     ap.add_argument("--sweeps", type=int, default=SWEEPS, help="sweeps per program (100 = the benchmark workload)")
     ap.add_argument("--hbm-log2", type=int, default=None,
                     help="--workload hbm: one loop of 2^k iterations only (default: 2^26 and 2^28)")
+    ap.add_argument("--bulk-mib", type=int, default=None,
+                    help="bulk arena of the context in MiB (the final fwrite's staging; library default 64)")
     ap.add_argument("--int-adds", type=int, default=None,
                     help="how many of the five neighbour adds run on the integer pipe (0..5; the program's "
                          "default when omitted)")
@@ -246,8 +248,9 @@ def main():
     gh = torch.from_numpy(g).pin_memory()
     stream = torch.cuda.Stream(device=dev)
     heap = 3 * N ** 3 * 8 + (256 << 20)
+    ckw = {} if args.bulk_mib is None else {"bulk_bytes": args.bulk_mib << 20}
     ctx = gf.Context(stream=stream, heap_bytes=heap, heap_small_pct=5,
-                     stdout_path=os.path.join(tmp, f"stdout_r{rank}.txt"))
+                     stdout_path=os.path.join(tmp, f"stdout_r{rank}.txt"), **ckw)
     argv = [N, sweeps, "-" if args.no_write else out_path]
     if args.int_adds is not None:
         argv.append(args.int_adds)

@@ -10,6 +10,7 @@
 #include <time.h>
 #include <unistd.h>
 
+#include <condition_variable>
 #include <thread>
 #include <chrono>
 #include <vector>
@@ -49,15 +50,91 @@ RecView::RecView(const uint8_t *r) : base(r)
 }
 
 /*
+ * Copy threads kept for the server's life.  A large write hands every thread
+ * one slice of the range and waits: creating and joining a dozen threads for
+ * every 32 MiB chunk cost more than the copy itself.  One job at a time (the
+ * server's output lock already serialises large writes).
+ */
+class CopyPool {
+  public:
+    CopyPool()
+    {
+        const unsigned hw = std::thread::hardware_concurrency();
+        nthr_ = hw < 4 ? 4 : hw > 16 ? 16 : hw;       /* page faults of distinct pages run in parallel */
+        for (unsigned t = 0; t < nthr_; t++)
+            th_.emplace_back([this, t] { loop(t); });
+    }
+    ~CopyPool()
+    {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : th_)
+            t.join();
+    }
+    void copy(unsigned char *dst, const unsigned char *src, uint64_t n)
+    {
+        std::unique_lock<std::mutex> lk(mu_);
+        dst_ = dst;
+        src_ = src;
+        n_ = n;
+        part_ = ((n + nthr_ - 1) / nthr_ + 4095) & ~4095ull;
+        pending_ = nthr_;
+        gen_++;
+        cv_.notify_all();
+        done_.wait(lk, [this] { return pending_ == 0; });
+    }
+
+  private:
+    void loop(unsigned t)
+    {
+        uint64_t seen = 0;
+        for (;;) {
+            unsigned char *dst;
+            const unsigned char *src;
+            uint64_t lo, len = 0;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+                if (stop_)
+                    return;
+                seen = gen_;
+                dst = dst_;
+                src = src_;
+                lo = (uint64_t)t * part_;
+                if (lo < n_)
+                    len = n_ - lo < part_ ? n_ - lo : part_;
+            }
+            if (len)
+                memcpy(dst + lo, src + lo, len);
+            std::lock_guard<std::mutex> g(mu_);
+            if (--pending_ == 0)
+                done_.notify_one();
+        }
+    }
+    unsigned nthr_ = 0;
+    std::vector<std::thread> th_;
+    std::mutex mu_;
+    std::condition_variable cv_, done_;
+    bool stop_ = false;
+    uint64_t gen_ = 0, n_ = 0, part_ = 0;
+    unsigned pending_ = 0;
+    unsigned char *dst_ = nullptr;
+    const unsigned char *src_ = nullptr;
+};
+
+/*
  * fwrite of a large buffer.  A single write(2) to one file copies into the
  * page cache on one thread (the kernel serialises writers of a file), which
  * is the bottleneck for a 128 MiB write.  For a regular file not opened for
- * append, the target range is mapped instead and several threads copy into
- * it (page faults of different pages proceed in parallel); the stdio
+ * append, the target range is mapped instead and the pool's threads copy
+ * into it (page faults of different pages proceed in parallel); the stdio
  * position is then moved past the data.  The bytes in the file are the same;
  * anything that is not a plain regular file, and small writes, use fwrite.
  */
-static size_t big_fwrite(const void *src, size_t size, size_t nmemb, FILE *f)
+size_t Server::big_fwrite(const void *src, size_t size, size_t nmemb, FILE *f)
 {
     const uint64_t n = (uint64_t)size * nmemb;
     const uint64_t min_par = 8ull << 20;
@@ -94,20 +171,9 @@ static size_t big_fwrite(const void *src, size_t size, size_t nmemb, FILE *f)
         close(rfd);
         return bad ? 0 : fwrite(src, size, nmemb, f);
     }
-    unsigned char *dst = (unsigned char *)m + (pos - mstart);
-    const unsigned hw = std::thread::hardware_concurrency();
-    const unsigned nthr = hw < 4 ? 4 : hw > 16 ? 16 : hw;   /* page faults of distinct pages run in parallel */
-    const uint64_t part = ((n + nthr - 1) / nthr + 4095) & ~4095ull;
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nthr; t++) {
-        const uint64_t lo = t * part;
-        if (lo >= n)
-            break;
-        const uint64_t len = n - lo < part ? n - lo : part;
-        th.emplace_back([=] { memcpy(dst + lo, (const unsigned char *)src + lo, len); });
-    }
-    for (auto &x : th)
-        x.join();
+    if (!pool_)
+        pool_.reset(new CopyPool());
+    pool_->copy((unsigned char *)m + (pos - mstart), (const unsigned char *)src, n);
     munmap(m, mlen);
     close(rfd);
     if (fseeko(f, end, SEEK_SET) != 0)

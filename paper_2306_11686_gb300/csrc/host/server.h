@@ -23,6 +23,7 @@
 #include <atomic>
 #include <functional>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <set>
 #include <string>
@@ -77,6 +78,8 @@ struct HostStats {
     }
 };
 
+class CopyPool;
+
 class Server {
   public:
     Server();
@@ -115,6 +118,8 @@ class Server {
     std::map<std::string, uint64_t> interned_;
     std::mutex user_mu_;
     std::map<uint32_t, std::pair<user_fn, void *>> user_;
+    std::unique_ptr<CopyPool> pool_;   /* copy threads of large writes, started on first use */
+    size_t big_fwrite(const void *src, size_t size, size_t nmemb, FILE *f);
 };
 
 /* record accessors (shared with tests) */
