@@ -366,8 +366,9 @@ int main(int argc, char **argv)
         S.join();
         fclose(out);
     } else if (sc == "bulkfile") {
-        /* large fwrite from the bulk arena (the parallel page-cache path for
-         * regular files, plain fwrite for append mode) after a small inline one */
+        /* two large fwrites from the bulk arena (the copy pool filling a shared
+         * mapping for regular files, plain fwrite for append mode) between
+         * small inline ones */
         const uint64_t len = (40ull << 20) + 3;
         std::vector<uint8_t> arena(len);
         for (uint64_t k = 0; k < len; k++)
@@ -386,20 +387,23 @@ int main(int argc, char **argv)
                 return fail("fopen");
             if (call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', 4, ""}, {'L', (uint64_t)fh, ""}, {'b', 0, "HEAD"}}) != 4)
                 return fail("inline fwrite");
-            if (call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', len, ""}, {'L', (uint64_t)fh, ""}, {'A', 0, ""},
-                                        {'L', len, ""}}) != (int64_t)len)
-                return fail("arena fwrite");
+            for (int rep = 0; rep < 2; rep++)   /* twice: the copy pool's second job, the position after the first */
+                if (call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', len, ""}, {'L', (uint64_t)fh, ""}, {'A', 0, ""},
+                                            {'L', len, ""}}) != (int64_t)len)
+                    return fail("arena fwrite");
             if (call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', 4, ""}, {'L', (uint64_t)fh, ""}, {'b', 0, "TAIL"}}) != 4)
                 return fail("inline fwrite after");
             if (call1(R, GF_OP_FCLOSE, {{'L', (uint64_t)fh, ""}}) != 0)
                 return fail("fclose");
             FILE *in = fopen(path.c_str(), "rb");
-            std::vector<uint8_t> got(len + 64);
+            std::vector<uint8_t> got(2 * len + 64);
             const size_t k = fread(got.data(), 1, got.size(), in);
             fclose(in);
             const size_t pre = !strcmp(mode, "ab") ? 3 : 0;
-            if (k != pre + 4 + len + 4 || memcmp(got.data() + pre, "HEAD", 4) ||
-                memcmp(got.data() + pre + 4, arena.data(), len) || memcmp(got.data() + pre + 4 + len, "TAIL", 4))
+            if (k != pre + 4 + 2 * len + 4 || memcmp(got.data() + pre, "HEAD", 4) ||
+                memcmp(got.data() + pre + 4, arena.data(), len) ||
+                memcmp(got.data() + pre + 4 + len, arena.data(), len) ||
+                memcmp(got.data() + pre + 4 + 2 * len, "TAIL", 4))
                 return fail(mode);
         }
         remove(path.c_str());
