@@ -121,6 +121,8 @@ typedef struct gf_stats {
     uint64_t copy_regions;        /* regions that moved large fwrite/fread data through the
                                      bulk arena (included in regions)                      */
     uint64_t copy_ns;             /* their device time (included in region_ns)             */
+    uint64_t host_ring_bytes;     /* ring bytes the host served: records written by the device,
+                                     8-byte returns read back (cumulative)                  */
 } gf_stats;
 
 /* Host landing pad for a user opcode (>= 256).  `rec` points at the lane

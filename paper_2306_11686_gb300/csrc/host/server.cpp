@@ -674,6 +674,7 @@ int Server::poll(Segment &seg, uint32_t tid, uint32_t nthr)
         stats.slots++;
         stats.records += nl;
         stats.ns += dt;
+        stats.ring_bytes += (uint64_t)(pay - slot) + 8ull * nl;
         stats.per_op[op < GF_NSTAT ? op : 0] += nl;
         seg.expect[s] = t + N;
         seg.cursor[tid] = (s + nthr) % N;

@@ -70,6 +70,7 @@ typedef int64_t (*user_fn)(void *user, uint32_t opcode, void *rec);
 
 struct HostStats {
     std::atomic<uint64_t> slots{0}, records{0}, ns{0}, dma_bytes{0};
+    std::atomic<uint64_t> ring_bytes{0};   /* slot bytes crossing the link: records in, returns out */
     std::atomic<uint64_t> per_op[GF_NSTAT];
     HostStats()
     {

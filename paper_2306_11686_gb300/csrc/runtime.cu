@@ -885,6 +885,7 @@ extern "C" GF_API int gf_wait(gf_handle *h, int *exit_code, int64_t timeout_ns)
         st.heap_ns = f.st_heap_ns;
         st.copy_regions = f.st_copy_regions;
         st.copy_ns = f.st_copy_ns;
+        st.host_ring_bytes = c->server.stats.ring_bytes;
     }
     if (rc == GF_OK && in->h_final.error)
         rc = in->h_final.error;

@@ -77,6 +77,7 @@ class gf_stats(ctypes.Structure):
         ("heap_ns", ctypes.c_uint64),
         ("copy_regions", ctypes.c_uint64),
         ("copy_ns", ctypes.c_uint64),
+        ("host_ring_bytes", ctypes.c_uint64),
     ]
 
     def as_dict(self):

@@ -68,10 +68,13 @@ def stress(args):
         with gf.Context(aggregate=agg, stream=stream, heap_bytes=8 << 30, heap_small_pct=95, server_threads=4,
                         stdout_path=os.path.join(tmp, "out.txt"), timeout_ns=int(120e9)) as ctx:
             _timed_run(ctx, stream, "printf_only", [1 << 14], [])          # warm-up
+            b0 = ctx.stats().host_ring_bytes
             t = _timed_run(ctx, stream, "printf_only", [T], [])
             st = ctx.stats()
             out[agg] = dict(calls_per_s=4 * T / t, seconds=t, p50_ns=st.rpc_p50_ns, p99_ns=st.rpc_p99_ns,
-                            slots=int(st.rpc_slots[gf.OP_PRINTF]), calls=int(st.rpc_calls[gf.OP_PRINTF]))
+                            slots=int(st.rpc_slots[gf.OP_PRINTF]), calls=int(st.rpc_calls[gf.OP_PRINTF]),
+                            ring_GBps=(st.host_ring_bytes - b0) / t / 1e9,
+                            ring_bytes_per_call=(st.host_ring_bytes - b0) / (4 * T))
             if agg:
                 hb = [(sizes, 1), (cs, 1), (fails, 1)]
                 _timed_run(ctx, stream, "heap_only", [T], hb)                # warm-up: slabs carved
