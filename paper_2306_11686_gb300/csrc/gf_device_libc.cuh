@@ -30,8 +30,6 @@
 #include "gf_device.cuh"
 #include "gf_strtod_fast.h"
 
-#define GF_OP_STRTOD_LIT GF_OP_STRTOD   /* the host strtod landing pad */
-
 namespace gfd {
 struct rand_state {
     int32_t r[34];               /* the last 31 (of 34) values, ring indexed by pos */
@@ -150,7 +148,7 @@ __device__ inline double gf_strtod(const char *str, char **endptr)
     /* exact slow path on the host: value bits returned, consumed length written back */
     long long used = 0;
     int st = 0;
-    const long long bits = gfd::rpc(GF_OP_STRTOD_LIT, nullptr, &st, str, gf_ref_write(&used, 8, 0));
+    const long long bits = gfd::rpc(GF_OP_STRTOD, nullptr, &st, str, gf_ref_write(&used, 8, 0));
     if (endptr)
         *endptr = (char *)str + (st == GF_OK ? used : 0);
     return st == GF_OK ? __longlong_as_double(bits) : 0.0;
