@@ -110,12 +110,13 @@ def test_jacobi_parity(gf_lib, oracle_bin, tmp_path, n, sweeps):
 
 
 @pytest.mark.parametrize("int_adds", [0, 1, 2, 3, 4, 5])
-@pytest.mark.parametrize("kind", ["unit", "signed", "tiny"])
+@pytest.mark.parametrize("kind", ["unit", "signed", "tiny", "huge", "ties", "smooth"])
 def test_jacobi_parity_every_pipe_split(gf_lib, oracle_bin, tmp_path, int_adds, kind):
     """Every split of the neighbour adds between the integer and FP64 pipes
     gives the serial program's bits: on the standard grid, on a grid of mixed
-    signs (opposite-sign adds take the FP64 path) and on one scaled down to
-    the subnormal range (so does every subnormal operand)."""
+    signs (opposite-sign adds take the FP64 path), on grids scaled into the
+    subnormal range and up by 2^200, on a constant interior (residuals tie)
+    and on a smooth grid whose residual grows along the iteration order."""
     import torch
     gf = gf_lib
     n, sweeps = 67, 5
@@ -124,6 +125,13 @@ def test_jacobi_parity_every_pipe_split(gf_lib, oracle_bin, tmp_path, int_adds, 
         g = np.where(g != 0.0, 2.0 * g - 1.0, 0.0)
     elif kind == "tiny":
         g = g * 2.0 ** -1060
+    elif kind == "huge":
+        g = g * 2.0 ** 200
+    elif kind == "ties":
+        g = np.where(g != 0.0, 0.5, 0.0)
+    elif kind == "smooth":
+        x = np.sin(np.pi * np.arange(n) / (n - 1))
+        g = np.where(g != 0.0, (x[:, None, None] * x[None, :, None] * x[None, None, :]).reshape(-1), 0.0)
     inputs.write_f64(tmp_path / "in.bin", g)
     want = oracle(oracle_bin, "jacobi", n, sweeps, tmp_path / "in.bin", tmp_path / "ref.bin")
     with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20,
