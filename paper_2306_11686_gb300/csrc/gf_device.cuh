@@ -400,6 +400,40 @@ template <class T, int OP, class F> __device__ void tramp_reduce(const gf_region
     finish_reduce(a, w);
 }
 
+/* The common case on its own: static schedule, chunk 1, fewer than 2^31
+ * iterations.  A trampoline holding only this loop, with a 32-bit induction
+ * variable (k + nthreads stays below 2^32), needs fewer registers than one
+ * holding every schedule, which keeps a register-hungry body free of spill
+ * reloads inside its loop. */
+__device__ __forceinline__ bool static1_fits(int sched, int64_t chunk, int64_t b, int64_t e)
+{
+    return sched == GF_SCHED_STATIC && chunk == 1 && e - b < (int64_t)0x7fffffff;
+}
+
+template <class G> __device__ __forceinline__ void run_static1(const gf_region *rd, const wctx &w, G &g)
+{
+    const int64_t b = rd->b;
+    const uint32_t n = (uint32_t)(rd->e - b), nth = (uint32_t)w.nthreads;
+#pragma unroll 2
+    for (uint32_t k = (uint32_t)w.tid; k < n; k += nth)
+        g(b + (int64_t)k);
+}
+
+template <class F> __device__ void tramp_for_s1(const gf_region *rd, const wctx &w)
+{
+    F f = *reinterpret_cast<const F *>(rd->body);
+    run_static1(rd, w, f);
+}
+
+template <class T, int OP, class F> __device__ void tramp_reduce_s1(const gf_region *rd, const wctx &w)
+{
+    F f = *reinterpret_cast<const F *>(rd->body);
+    acc<T, OP> a;
+    auto g = [&](int64_t i) { a.add((T)f(i)); };
+    run_static1(rd, w, g);
+    finish_reduce(a, w);
+}
+
 /* ------------------------------------------------------------ region launch (initial thread) */
 /* kernel split: ask the host to launch the region kernel; its grid, or < 0 */
 static __device__ int64_t split_launch(gf_state *S, int *status);
@@ -529,7 +563,7 @@ __device__ int gf_parallel_for(int64_t b, int64_t e, int sched, int64_t chunk, F
         return GF_OK;
     gf_state *S = gfd::s_st;
     gf_region *r = &S->region;
-    r->fn = (uint64_t)(&gfd::tramp_for<F>);
+    r->fn = gfd::static1_fits(sched, chunk, b, e) ? (uint64_t)(&gfd::tramp_for_s1<F>) : (uint64_t)(&gfd::tramp_for<F>);
     r->b = b;
     r->e = e;
     r->chunk = chunk;
@@ -554,7 +588,8 @@ __device__ int gf_reduce(int64_t b, int64_t e, int sched, int64_t chunk, F body,
     }
     gf_state *S = gfd::s_st;
     gf_region *r = &S->region;
-    r->fn = (uint64_t)(&gfd::tramp_reduce<T, OP, F>);
+    r->fn = gfd::static1_fits(sched, chunk, b, e) ? (uint64_t)(&gfd::tramp_reduce_s1<T, OP, F>)
+                                                  : (uint64_t)(&gfd::tramp_reduce<T, OP, F>);
     r->b = b;
     r->e = e;
     r->chunk = chunk;

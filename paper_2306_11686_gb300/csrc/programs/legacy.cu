@@ -68,9 +68,11 @@ __device__ int jacobi_sweep(const double *u, double *un, uint32_t nn, uint64_t c
         0, (int64_t)cells, GF_SCHED_STATIC, 1,
         [=](int64_t c64) -> double {
             const uint32_t c = (uint32_t)c64;
-            const uint32_t jk = dn.div(c), i = c - jk * nn;
-            const uint32_t k = dn.div(jk), j = jk - k * nn;
-            if (i == 0 || j == 0 || k == 0 || i == nn - 1 || j == nn - 1 || k == nn - 1) {
+            /* i - 1, j - 1, k - 1 wrap to 2^32 - 1 at 0, so one unsigned
+             * compare of their maximum finds every boundary cell */
+            const uint32_t jk = dn.div(c), im1 = c - 1u - jk * nn;
+            const uint32_t k = dn.div(jk), jm1 = jk - 1u - k * nn;
+            if (max(im1, max(jm1, k - 1u)) >= nn - 2u) {
                 un[c] = 0.0;
                 return 0.0;
             }

@@ -89,7 +89,7 @@ def test_axpy_host_buffers_e2e(gf_lib, oracle_bin, tmp_path):
     assert np.array_equal(yh, np.fromfile(tmp_path / "ref.bin"))
 
 
-@pytest.mark.parametrize("n,sweeps", [(3, 2), (8, 3), (18, 4), (67, 5), (256, 100)])
+@pytest.mark.parametrize("n,sweeps", [(1, 2), (2, 2), (3, 2), (8, 3), (18, 4), (67, 5), (256, 100)])
 def test_jacobi_parity(gf_lib, oracle_bin, tmp_path, n, sweeps):
     import torch
     gf = gf_lib
