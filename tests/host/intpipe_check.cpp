@@ -1,7 +1,8 @@
 /* Host build of the integer-pipe FP64 helpers compared with the host's IEEE
- * arithmetic: gf_dadd_int(x, y) against x + y (bits, NaN as NaN) over
- * same-sign pairs at every exponent gap, round-to-even ties, carries into the
- * next binade, zeros, subnormals, overflow and random bit patterns;
+ * arithmetic: gf_dadd_int(x, y) and gf_dadd_int_any(x, y) against x + y
+ * (bits, NaN as NaN) over same-sign pairs at every exponent gap,
+ * round-to-even ties, carries into the next binade, zeros, subnormals,
+ * overflow and random bit patterns;
  * gf_udiv32 against '/' over edge and random operands (exhaustive over
  * [0, 2^31) for two divisors).  Prints "<name> checked N mismatches M". */
 #include <cmath>
@@ -18,13 +19,17 @@ static void add_case(double x, double y)
 {
     volatile double vx = x, vy = y;
     const double want = vx + vy;
-    const double got = gf_dadd_int(x, y);
-    n_add++;
-    const bool ok = (std::isnan(want) && std::isnan(got)) || B(want) == B(got);
-    if (!ok) {
-        if (bad_add < 10)
-            printf("dadd mismatch %a + %a: got %a want %a\n", x, y, got, want);
-        bad_add++;
+    /* the entry point (short path for small exponent gaps) and the
+     * any-gap path on its own */
+    const double got[2] = {gf_dadd_int(x, y), gf_dadd_int_any(x, y)};
+    for (int p = 0; p < 2; p++) {
+        n_add++;
+        const bool ok = (std::isnan(want) && std::isnan(got[p])) || B(want) == B(got[p]);
+        if (!ok) {
+            if (bad_add < 10)
+                printf("dadd%s mismatch %a + %a: got %a want %a\n", p ? "_any" : "", x, y, got[p], want);
+            bad_add++;
+        }
     }
 }
 
@@ -56,6 +61,15 @@ int main(int argc, char **argv)
             add_case(x, D(B(h) - 1));
             add_case(-x, -h);
         }
+    }
+    /* exponent gaps 1..10 whose dropped bits are exactly one half: the ties
+     * of the short path, with and without a carry into the next binade */
+    for (long it = 0; it < 200000 * scale; it++) {
+        const uint64_t d = 1 + rng() % 10, ea = 20 + rng() % 2020;
+        const uint64_t low = (1ull << d) - 1;
+        const uint64_t fb = (u53() & ~low) | (1ull << (d - 1));
+        add_case(D((ea << 52) | u53()), D(((ea - d) << 52) | fb));
+        add_case(D(((ea - d) << 52) | fb), D((ea << 52) | u53()));
     }
     /* carries into the next binade, and all-ones significands */
     for (long it = 0; it < 100000 * scale; it++) {

@@ -285,7 +285,7 @@ def test_div6_matches_ieee_division(gf_lib, ctx):
 
 def test_dadd_int_matches_fp64_add(gf_lib, ctx):
     """gf_dadd_int (same-sign add on the integer pipe) equals the FP64 add bit
-    for bit on the GPU: every exponent gap, ties, carries, the Jacobi range,
+    for bit on the GPU: every exponent gap, ties (of both paths), carries, the Jacobi range,
     zeros, subnormals, overflow, NaN/inf and random bit patterns."""
     import torch
     rng = np.random.default_rng(8)
@@ -301,10 +301,19 @@ def test_dadd_int_matches_fp64_add(gf_lib, ctx):
     tx = (ties_e << np.uint64(52)) | frac(q)
     th = ((ties_e - np.uint64(53)) << np.uint64(52)) + rng.integers(-1, 2, q).astype(np.uint64)
     ones = (ea << np.uint64(52)) | np.uint64((1 << 52) - 1)
+    # exponent gaps 1..10 with the dropped bits exactly one half (ties of the short path)
+    dg = rng.integers(1, 11, q).astype(np.uint64)
+    se = rng.integers(20, 2040, q).astype(np.uint64)
+    low = (np.uint64(1) << dg) - np.uint64(1)
+    sfrac = (frac(q) & ~low) | (np.uint64(1) << (dg - np.uint64(1)))
+    sx_ = (se << np.uint64(52)) | frac(q)
+    sy_ = ((se - dg) << np.uint64(52)) | sfrac
+    xa = np.concatenate([xa, sx_])
+    xb = np.concatenate([xb, sy_])
     x = np.concatenate([xa.view(np.float64), tx.view(np.float64), ones.view(np.float64),
                         rng.random(q) * 6.0, rng.integers(0, 2 ** 63, q, dtype=np.uint64).view(np.float64) *
                         np.where(rng.random(q) < 0.5, -1.0, 1.0)])
-    y = np.concatenate([xb.view(np.float64), th.view(np.float64), xb.view(np.float64) * np.sign(ones.view(np.float64)),
+    y = np.concatenate([xb.view(np.float64), th.view(np.float64), xb[:q].view(np.float64) * np.sign(ones.view(np.float64)),
                         rng.random(q) * 6.0, rng.integers(0, 2 ** 64, q, dtype=np.uint64).view(np.float64)])
     special = np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, np.nan, 5e-324, -5e-324, 2.2250738585072014e-308,
                         1.7976931348623157e308, float.fromhex("0x1.fffffffffffffp1022"), 2.0 ** 1023, 3.0])
