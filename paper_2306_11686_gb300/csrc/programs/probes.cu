@@ -63,6 +63,31 @@ GF_MAIN(reduce_probe)(int argc, char **argv)
     return rc ? 10 : 0;
 }
 
+/* range_probe b e                  buffer 0 = int64 out[4]
+ * Static chunk-1 loops over [b, e) with a large base: the count, the sum of
+ * i - b, min and max of i, as integer reductions (a trampoline of its own
+ * below 2^31 iterations, the generic 64-bit loop above). */
+GF_MAIN(range_probe)(int argc, char **argv)
+{
+    if (argc < 3)
+        return 2;
+    const long long b = gf_atoll(argv[1]), e = gf_atoll(argv[2]);
+    long long *out = (long long *)gf_buffer(0);
+    if (!out)
+        return 2;
+    long long r;
+    int rc = 0;
+    rc |= gf_reduce<long long, GF_RED_SUM>(b, e, GF_SCHED_STATIC, 1, [=](int64_t i) { return 1ll; }, &r);
+    out[0] = r;
+    rc |= gf_reduce<long long, GF_RED_SUM>(b, e, GF_SCHED_STATIC, 1, [=](int64_t i) { return (long long)(i - b); }, &r);
+    out[1] = r;
+    rc |= gf_reduce<long long, GF_RED_MIN>(b, e, GF_SCHED_STATIC, 1, [=](int64_t i) { return (long long)i; }, &r);
+    out[2] = r;
+    rc |= gf_reduce<long long, GF_RED_MAX>(b, e, GF_SCHED_STATIC, 1, [=](int64_t i) { return (long long)i; }, &r);
+    out[3] = r;
+    return rc ? 10 : 0;
+}
+
 /* barrier_probe rounds             buffers: 0 = int64 a[T], 1 = int64 errors[1]
  * Each worker writes its slot, crosses the grid barrier, and reads a slot
  * written by a thread of another block; any stale value counts an error. */

@@ -54,6 +54,20 @@ def test_schedules(gf_lib, ctx, b, e, sched, chunk):
         assert o.min() >= 0 and o.max() < T
 
 
+@pytest.mark.parametrize("b,n", [(1 << 40, 1000), (1 << 40, (1 << 31) - 2), (-(1 << 35), (1 << 31) + 7)])
+def test_static1_ranges(gf_lib, ctx, b, n):
+    """Static chunk-1 loops with a large (or negative) base, on both sides of
+    2^31 iterations: below it they run in the 32-bit trampoline, above it in
+    the generic 64-bit loop.  Every index is visited once: the count, the
+    sum of i - b, min and max of i."""
+    import torch
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    rc, ec = ctx.run("range_probe", [b, b + n], [(out, 1)])
+    assert ec == 0
+    o = out.cpu().tolist()
+    assert o == [n, n * (n - 1) // 2, b, b + n - 1]
+
+
 @pytest.mark.parametrize("n,sched,chunk", [(1, 0, 1), (1000, 0, 1), (1 << 20, 0, 1), (123457, 1, 5), (99, 0, 0)])
 def test_reductions(gf_lib, ctx, n, sched, chunk):
     import torch
