@@ -4,7 +4,7 @@
  *
  * Exactly rounded sum of binary64 values.  The paper leaves reductions in
  * multi-team regions unimplemented (Sec. 4.3), so the reduction added here is
- * judged against the plain definition: the real-number sum of the inputs,
+ * checked against the plain definition: the real-number sum of the inputs,
  * rounded once to nearest-even.  The method is a Kulisch-style long
  * accumulator: every finite double is m * 2^e with an integer |m| < 2^53 and
  * e >= -1074, so all of them are integers in units of 2^-1074 and their sum is

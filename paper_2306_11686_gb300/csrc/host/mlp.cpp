@@ -4,7 +4,7 @@
  * The model maps (loop features, shape features) to a predicted log of the
  * loop's run time; the chosen shape is the argmin over the candidate set.
  * The autotuner (exhaustive measurement over the same set) is the fallback
- * and the judge of the model's regret.
+ * and the yardstick of the model's regret.
  */
 #include <math.h>
 #include <stdint.h>
