@@ -34,8 +34,8 @@ N, SWEEPS = 256, 100
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_OPS_PER_POINT = 7
 # DRAM bytes (read + write) of one full launch, scaled from an ncu capture of
-# 20 sweeps without the final write (profiles/jacobi_256_sweeps_ncu.md):
-# 314.1 MB per sweep x 100 + the 134.2 MB read of the final fwrite.
+# 20 sweeps without the final write: 314.1 MB per sweep x 100 + the 134.2 MB
+# read of the final fwrite.
 TRAFFIC_PER_LAUNCH = 100 * 314_124_500 + 134_217_728
 
 
