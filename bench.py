@@ -360,7 +360,7 @@ def main():
                                  "algorithmic_bytes_per_launch": launch_bytes,
                                  "sweeps_only": round(loop_bytes(N, 1) / sweep_s / 1e9, 1)}},
             "e2e": None if e2e is None else {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": N ** 3 * 8,
-                    "d2h_bytes_per_step": N ** 3 * 8 + 100 * 24},
+                    "d2h_bytes_per_step": N ** 3 * 8 + 100 * 24, "steps": e2e_steps, "warmup": 1},
             "gpu_launches": args.steps,
             "cpu_baseline": cpu,
             "cpu_openmp": cpu_omp,
