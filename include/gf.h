@@ -315,11 +315,14 @@ GF_API int gf_grid_info(gf_ctx *ctx, gf_program prog, uint32_t *sms, uint32_t *b
  *
  * *out (device) = op over x[0 .. n) (device FP64), op one of GF_REDUCE_SUM,
  * GF_REDUCE_MIN, GF_REDUCE_MAX, computed by the same reduction a gf_reduce
- * region uses (compensated per-thread sums, warp / block trees, last block
- * combines the per-block partials in block order), launched on `stream`
- * (cudaStream_t, NULL = legacy default) and not waited for.  blocks = 0
- * picks SMs x resident blocks; at most 2048 blocks (larger: GF_EINVAL).
- * n = 0 stores the identity (0, +inf, -inf).
+ * region uses (compensated per-thread sums, warp / block trees, one partial
+ * per block; the last block merges the partials with a strided per-thread
+ * pass and the same warp / block trees), launched on `stream` (cudaStream_t,
+ * NULL = legacy default) and not waited for.  blocks = 0 picks SMs x
+ * resident blocks; at most 2048 blocks (larger: GF_EINVAL).  n = 0 stores
+ * the identity (0, +inf, -inf).  MIN and MAX are exact.  A SUM is the same
+ * bits on every run with the same `blocks`; the default grid differs between
+ * GPU models, so pass `blocks` to get identical bits everywhere.
  *
  * Nothing is allocated: the per-block partials live in one static device
  * array of 32 KiB + 256 B inside this library, present on every GPU that
@@ -330,7 +333,8 @@ GF_API int gf_grid_info(gf_ctx *ctx, gf_program prog, uint32_t *sms, uint32_t *b
  * address up (cudaGetSymbolAddress, with that device current) and caches it;
  * make that first call before any stream capture starts.
  * Errors: GF_EINVAL (bad op, n < 0, NULL pointers, too many blocks),
- * GF_ECUDA (lookup or launch failed). */
+ * GF_ECUDA (lookup, ticket clear or launch failed).  A CUDA error left
+ * pending by the caller's earlier work is not read or cleared. */
 #define GF_REDUCE_SUM 1
 #define GF_REDUCE_MIN 2
 #define GF_REDUCE_MAX 3

@@ -9,11 +9,16 @@
  * per-instance state).  Such callers pass their input and output buffers and
  * nothing else is allocated on their behalf.
  *
- * Same algorithm as a gf_reduce region (per-thread accumulation with Neumaier
- * compensation for sums, xor-shuffle warp tree, shared-memory block tree, one
- * partial per block, the last block combines the partials in block order),
- * but the per-block partials and the last-block ticket live in one file-scope
- * device array, gf_noalloc_scratch, instead of context memory.
+ * Same algorithm as a gf_reduce region: per-thread accumulation (Neumaier
+ * compensation for sums), xor-shuffle warp tree, shared-memory block tree, one
+ * partial per block; the last block to finish merges the partials with a
+ * strided per-thread pass (thread t takes partials t, t + 256, ...) followed
+ * by the same warp and block trees.  The per-block partials and the
+ * last-block ticket live in one file-scope device array, gf_noalloc_scratch,
+ * instead of context memory.  The combine order depends only on the grid, so
+ * a SUM gives the same bits on every run with the same `blocks`; the default
+ * grid follows the device (SMs x occupancy), so callers that need identical
+ * bits on every GPU pass `blocks` explicitly.
  *
  * Limits and sharing:
  *  - at most GF_NOALLOC_MAX_BLOCKS blocks (the scratch holds one 16-byte
@@ -152,11 +157,12 @@ extern "C" GF_API int gf_reduce_f64_noalloc(const double *x, int64_t n, int op, 
     unsigned char *scr = (unsigned char *)d.scratch;
     if (cudaMemsetAsync(scr + GF_NOALLOC_MAX_BLOCKS * 16, 0, sizeof(unsigned), s) != cudaSuccess)
         return GF_ECUDA;
-    if (op == GF_RED_SUM)
-        noalloc_reduce_kernel<GF_RED_SUM><<<grid, 256, 0, s>>>(x, n, out, scr);
-    else if (op == GF_RED_MIN)
-        noalloc_reduce_kernel<GF_RED_MIN><<<grid, 256, 0, s>>>(x, n, out, scr);
-    else
-        noalloc_reduce_kernel<GF_RED_MAX><<<grid, 256, 0, s>>>(x, n, out, scr);
-    return cudaGetLastError() == cudaSuccess ? GF_OK : GF_ECUDA;
+    /* cudaLaunchKernel reports this launch's own status: an error left
+     * pending on the caller's thread by earlier work is neither read nor
+     * cleared here */
+    const void *fn = op == GF_RED_SUM   ? (const void *)noalloc_reduce_kernel<GF_RED_SUM>
+                     : op == GF_RED_MIN ? (const void *)noalloc_reduce_kernel<GF_RED_MIN>
+                                        : (const void *)noalloc_reduce_kernel<GF_RED_MAX>;
+    void *args[4] = {(void *)&x, (void *)&n, (void *)&out, (void *)&scr};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(256), args, 0, s) == cudaSuccess ? GF_OK : GF_ECUDA;
 }
