@@ -32,11 +32,36 @@ sys.path.insert(0, ROOT)
 
 N, SWEEPS = 256, 100
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 operations of the serial program per interior point: 5 neighbour adds,
+# the division by 6, the residual's subtract.
 FP64_OPS_PER_POINT = 7
-# DRAM bytes (read + write) of one full launch, scaled from an ncu capture of
-# 20 sweeps without the final write: 314.1 MB per sweep x 100 + the 134.2 MB
-# read of the final fwrite.
-TRAFFIC_PER_LAUNCH = 100 * 314_124_500 + 134_217_728
+# DRAM bytes (read + write) of one full launch from an ncu capture of the
+# current program kernel, or None when the kernel changed since the capture.
+TRAFFIC_PER_LAUNCH = None
+
+
+def fp64_pipe_ops_per_point(int_adds):
+    """Operations per interior point that issue on the FP64 pipe: the
+    neighbour adds left to it, plus the residual's subtract.  The division by 6,
+    the absolute value and `int_adds` of the five adds run on the integer pipe."""
+    return (5 - int_adds) + 1
+
+
+def fp64_add_peak(gf, stream, tries=5, iters=8192):
+    """The measured FP64 add rate of this GPU (gf_fp64_add_rate: eight
+    independent add chains per thread, CUDA events), best of `tries`, with the
+    SM clock sampled while it runs."""
+    import ctypes
+    best = 0.0
+    with Clocks() as clk:
+        for _ in range(tries):
+            ms, adds = ctypes.c_float(), ctypes.c_double()
+            rc = gf.gf_fp64_add_rate(0, iters, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(ms),
+                                     ctypes.byref(adds))
+            if rc != gf.GF_OK:
+                raise gf.GFError(rc, "gf_fp64_add_rate")
+            best = max(best, adds.value / (ms.value / 1e3))
+    return best, clk.summary()
 
 
 def max_over_ranks(seconds, world, device):
@@ -213,6 +238,9 @@ def main():
                     help="how many of the five neighbour adds run on the integer pipe (0..5; the program's "
                          "default when omitted)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the same-process extra measurements (printf calls/s with and without warp "
+                         "aggregation, one axpy loop at 2^28 against HBM, the measured FP64 add peak)")
     ap.add_argument("--no-write", action="store_true",
                     help="the program skips its final fwrite (profiling runs that isolate the sweeps)")
     ap.add_argument("--workload", default="jacobi", choices=["jacobi", "stress", "batch", "learned", "serve", "e1", "link", "hbm", "split"],
@@ -290,7 +318,7 @@ def main():
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e2e_steps = max(1, min(args.steps, 3))
+        e2e_steps = args.steps
         step(gh)            # warm-up: the first host-buffer run maps its staging allocation
         torch.cuda.synchronize(dev)
         e0.record(stream)
@@ -309,20 +337,35 @@ def main():
     achieved = launch_bytes / (total / args.steps) / 1e9
     # the program's own regions (the sweeps), without the final fwrite's copies
     sweep_s = max(st.region_ns - st.copy_ns, 1) / max(1, st.regions - st.copy_regions) / 1e9
-    # The sweep's binding roofline is FP64 arithmetic, not HBM: GB300 retires
-    # 2 FP64 lanes per clock per SM, and 7 FP64 operations per interior point
-    # (5 adds, the /6, the residual's subtract) need 4.6x longer on that pipe
-    # than the point's 16 bytes need on HBM.  The program moves part of the
-    # operations to the integer pipe (bit-identical results), so the fraction
-    # of the FP64 peak can read a little above 1.  HBM is reported beside it.
+    # The sweep's binding roofline is the FP64 pipe, not HBM: GB300 retires
+    # FP64 adds at a small fraction of its other rates, and the serial
+    # program's 7 FP64 operations per interior point need several times longer
+    # on that pipe than the point's 16 bytes need on HBM.  The program runs
+    # the division by 6, the absolute value and one of the five adds on the
+    # integer pipe (bit-identical results), so the roofline counts what
+    # issues on the FP64 pipe -- the other four adds and the residual's
+    # subtract -- against the FP64 add rate measured on this GPU in this run.
+    # HBM is reported beside it.
     sms = ctx.grid_info("jacobi")[0]
-    sm_mhz = 2070.0
-    try:
-        sm_mhz = float(json.load(open(PEAKS)).get("sm_max_mhz", sm_mhz))
-    except Exception:
-        pass
-    fp64_peak = sms * 2 * sm_mhz * 1e6                               # FP64 operations / s
-    fp64_ops = FP64_OPS_PER_POINT * (N - 2) ** 3 * sweeps
+    int_adds = 1 if args.int_adds is None else args.int_adds
+    pipe_per_point = fp64_pipe_ops_per_point(int_adds)
+    fp64_peak, peak_clocks = fp64_add_peak(gf, stream)                     # FP64 adds / s
+    fp64_ops = pipe_per_point * (N - 2) ** 3 * sweeps
+    extra = None
+    if rank == 0 and not args.no_extra:
+        from paper_2306_11686_gb300 import measure
+        ax = measure.axpy_regions((28,))["2^28"]
+        extra = {"fp64_peak": {"adds_per_s": round(fp64_peak), "per_sm_per_clock":
+                               round(fp64_peak / (sms * peak_clocks["sm_mhz"] * 1e6), 3)
+                               if peak_clocks.get("sm_mhz") else None,
+                               "clocks": peak_clocks,
+                               "how": "gf_fp64_add_rate: SMs x resident blocks of 256 threads, 8 independent "
+                                      "add.rn.f64 chains x 8192 per thread, CUDA events, best of 5"},
+                 "hbm": {"workload": "one axpy loop z = 2.5 x + y, N = 2^28, one static chunk-1 region "
+                                     "through the plain runtime (24 B per iteration, 6.4 GB)",
+                         "GBps": round(ax["GBps"], 1), "frac": round(ax["GBps"] / peak, 4),
+                         "peak": peak, "peak_kind": peak_kind, "correct": ax["correct"]},
+                 "stress": measure.printf_rate(1 << 20, out_dir=out_dir)}
     cpu = cpu_omp = None
     if rank == 0 and args.cpu_sweeps > 0:
         cv, cdt, cc, pinned = cpu_oracle_sample(N, args.cpu_sweeps, tmp)
@@ -345,13 +388,19 @@ def main():
                        "output": None if args.no_write else {"dir": os.path.dirname(tmp), "fs": fs_type(tmp)},
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "achieved": round(fp64_ops / (total / args.steps) / 1e9, 1),
-                         "peak": round(fp64_peak / 1e9, 1), "unit": "G FP64 op/s",
+                         "peak": round(fp64_peak / 1e9, 1), "unit": "G FP64 add/s",
                          "frac": round(fp64_ops / (total / args.steps) / fp64_peak, 4),
                          "traffic": TRAFFIC_PER_LAUNCH,
-                         "peak_kind": f"derived: {sms} SMs x 2 FP64 lanes/clock x {sm_mhz:.0f} MHz",
+                         "peak_kind": "measured: gf_fp64_add_rate in this run (extra.fp64_peak), "
+                                      f"sampled SM clock {peak_clocks.get('sm_mhz')} MHz",
                          "kernel": "program_kernel<jacobi>",
-                         "algorithmic": f"{FP64_OPS_PER_POINT} FP64 operations per interior point (5 adds, the /6, "
-                                        f"the residual's subtract) x {N - 2}^3 x {sweeps} sweeps",
+                         "algorithmic": f"{pipe_per_point} FP64-pipe operations per interior point ({5 - int_adds} "
+                                        f"neighbour adds + the residual's subtract) x {N - 2}^3 x {sweeps} sweeps; "
+                                        f"the /6, |.| and {int_adds} add(s) run on the integer pipe",
+                         "all_fp64_ops": {"per_point": FP64_OPS_PER_POINT,
+                                          "on_integer_pipe": int_adds + 1,
+                                          "achieved": round(FP64_OPS_PER_POINT * (N - 2) ** 3 * sweeps /
+                                                            (total / args.steps) / 1e9, 1)},
                          "sweeps_only": {"achieved": round(fp64_ops / sweeps / sweep_s / 1e9, 1),
                                          "frac": round(fp64_ops / sweeps / sweep_s / fp64_peak, 4),
                                          "sweep_us": round(sweep_s * 1e6, 2)},
@@ -365,6 +414,7 @@ def main():
             "cpu_baseline": cpu,
             "cpu_openmp": cpu_omp,
             "clocks": clk.summary(),
+            "extra": extra,
             "detail": {"main_ns": st.main_ns, "regions": st.regions, "region_ns": st.region_ns,
                        "sweep_us": round(sweep_s * 1e6, 2),
                        "sweep_GBps": round(loop_bytes(N, 1) / sweep_s / 1e9, 1),

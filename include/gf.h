@@ -301,6 +301,15 @@ GF_API int gf_mlp_topk(const float *params, int width, int depth, const gf_synth
 GF_API int gf_alloc_e1(gf_ctx *ctx, int kind, uint32_t teams, uint32_t threads, uint32_t bytes, int reps,
                        void *stream, float *ms, uint64_t *fails);
 
+/* The FP64 add throughput of the current device, for the roofline of FP64-bound
+ * loops (the Jacobi sweep).  A kernel of `blocks` x 256 threads (0 = SMs x
+ * resident blocks), each running eight independent chains of `iters`
+ * correctly rounded FP64 adds, runs once to warm up and once timed with CUDA
+ * events on `stream`.  *ms = the timed run, *adds = FP64 adds it issued
+ * (thread count x iters x 8), so *adds / *ms is the measured rate at the
+ * clock the GPU ran during the call.  Errors: GF_EINVAL, GF_ECUDA. */
+GF_API int gf_fp64_add_rate(uint32_t blocks, int64_t iters, void *stream, float *ms, double *adds);
+
 /* Number of SMs and resident blocks per SM that a program's grid uses at
  * `block` threads (for sizing, tests and roofline accounting). */
 GF_API int gf_grid_info(gf_ctx *ctx, gf_program prog, uint32_t *sms, uint32_t *blocks_per_sm);

@@ -23,7 +23,7 @@ NVFLAGS = ARCH + INC + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcom
                         "-Xptxas", "-v", "-diag-suppress", "177"]
 CXXFLAGS = INC + ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-Wall"]
 
-CU = ["runtime.cu", "noalloc.cu", "programs/legacy.cu", "programs/probes_sched.cu", "programs/probes_rpc.cu",
+CU = ["runtime.cu", "noalloc.cu", "peak.cu", "programs/legacy.cu", "programs/probes_sched.cu", "programs/probes_rpc.cu",
       "programs/probes_heap.cu", "programs/probes_misc.cu", "programs/stress.cu", "programs/batch.cu",
       "programs/synth.cu", "programs/serve.cu",
       "programs/alloc_e1.cu", "programs/libc.cu"]

@@ -787,6 +787,7 @@ __global__ void __launch_bounds__(GF_BLOCK, MINB) program_kernel(gf_state *S, in
         if (threadIdx.x == 0) {
             S->t_main_start = now_ns();
             int rc = MAIN(argc, argv);
+            rpc_collect_deferred(S);     /* a printf main did not wait for */
             S->exit_code = rc;
             S->t_main_end = now_ns();
             S->main_done = 1;

@@ -19,6 +19,19 @@
  * host by device address afterwards (the paper copies them on every call).
  * A format string must therefore not change while the context lives (string
  * literals are the intended use).
+ *
+ * Deferred calls: a printf-family call from the initial thread is published
+ * without waiting for the host.  Its result comes back as a gf_call_result,
+ * which waits when it is converted to int; a call whose result the program
+ * never reads is collected (waited for, its slot given back) at the initial
+ * thread's next RPC or when main returns.  At most one call is outstanding,
+ * so the initial thread's calls still reach the host in program order, and
+ * the serial part runs on (the next sweep, say) while the host formats the
+ * text.  Calls from a region's threads complete before they return.
+ *
+ * After the first device-side error of a program (a ring or reply timeout),
+ * every later call fails at once with that error instead of waiting out its
+ * own timeout on a slot the host may still be writing into.
  */
 #ifndef GF_DEVICE_RPC_CUH
 #define GF_DEVICE_RPC_CUH
@@ -196,21 +209,70 @@ __device__ inline void fmt_insert(gf_state *S, uint64_t key)
 }
 
 /*
+ * The initial thread's outstanding deferred call: wait (bounded) until the
+ * host has answered it, keep its result in the state, give its slot back.
+ * Initial thread only.
+ */
+static __device__ __noinline__ int rpc_collect_deferred(gf_state *S)
+{
+    const unsigned long long t1 = S->pend_ticket1;
+    if (!t1)
+        return GF_OK;
+    const unsigned long long t = t1 - 1;
+    S->pend_ticket1 = 0;
+    uint8_t *slot = (uint8_t *)(S->ring_slots + (t % S->nslots) * (uint64_t)S->slot_bytes);
+    gf_slot_hdr *h = (gf_slot_hdr *)slot;
+    const uint64_t t0 = now_ns();
+    backoff bo(S->timeout_ns);
+    while (ld_acq_sys64(&h->seq) != t + 2)
+        if (!bo.wait()) {
+            set_error(GF_ETIMEDOUT);
+            S->done_ticket1 = t1;
+            S->done_val = -1;
+            return GF_ETIMEDOUT;
+        }
+    S->done_val = (int64_t)ld_vol64((const uint64_t *)(slot + GF_SLOT_RET_OFF));
+    S->done_ticket1 = t1;
+    const uint32_t op = h->opcode;
+    S->st_wait_ns += now_ns() - t0;
+    S->st_calls[op < GF_NSTAT ? op : 0]++;
+    S->st_slots[op < GF_NSTAT ? op : 0]++;
+    if (S->pend_fmt_key)
+        fmt_insert(S, S->pend_fmt_key);
+    st_rel_sys64(&h->seq, t + S->nslots);
+    return GF_OK;
+}
+
+/*
  * Issue one RPC from every calling lane; returns this lane's host result.
  * *status receives GF_OK, GF_ERING (no slot credit within the timeout),
- * GF_ETIMEDOUT (host did not answer) or GF_EINVAL (record larger than a slot).
+ * GF_ETIMEDOUT (host did not answer), GF_EINVAL (record larger than a slot)
+ * or the program's first error when one was already recorded.
+ * defer_t1 (initial thread only): publish without waiting; *defer_t1
+ * receives the ticket + 1 to collect later, and the return value is 0.
  */
-static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, const argpack &a, int *status)
+static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, const argpack &a, int *status,
+                                                 unsigned long long *defer_t1 = nullptr)
 {
     gf_state *S = s_st;
     const uint32_t lane = lane_id();
     const uint32_t active = __activemask();
+    if (is_initial_thread() && S->pend_ticket1)      /* keep the initial thread's calls in order */
+        rpc_collect_deferred(S);
+    {
+        /* fail fast after the first error; one reading for the whole group */
+        const int err = __shfl_sync(active, *(volatile int32_t *)&S->error, __ffs(active) - 1);
+        if (err) {
+            if (status)
+                *status = err;
+            return -1;
+        }
+    }
     const uint64_t key = (uint64_t)fmt;
     const uint64_t sig = a.signature(op, key);
     const uint32_t grp = S->aggregate ? __match_any_sync(active, sig) : (1u << lane);
     const uint32_t my = a.bytes();
     const uint32_t gtid = is_initial_thread() ? 0xffffffffu : (uint32_t)gf_thread_num();
-    const uint32_t fmt_len = fmt ? gf_strlen(fmt) + 1u : 0u;
     const uint32_t slot_cap = S->slot_bytes - GF_SLOT_PAYLOAD_OFF;
 
     uint32_t remaining = grp;
@@ -221,9 +283,13 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
         /* format shipping is decided once per round by its leader */
         const uint32_t rl = __ffs(remaining) - 1;
         int ship = 0;
-        if (lane == rl)
+        uint32_t fmt_len = 0;
+        if (lane == rl) {
             ship = (fmt && !fmt_known(S, key)) ? 1 : 0;
+            fmt_len = ship ? gf_strlen(fmt) + 1u : 0u;      /* read the format only to ship it */
+        }
         ship = __shfl_sync(grp, ship, rl);
+        fmt_len = __shfl_sync(grp, fmt_len, rl);
         const uint32_t fbytes = ship ? ((fmt_len + 7u) & ~7u) : 0u;
         const uint32_t cap = slot_cap > fbytes ? slot_cap - fbytes : 0u;
         /* exclusive prefix of record sizes over the lanes still waiting */
@@ -304,6 +370,16 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
         __threadfence_system();
         __syncwarp(grp);
         int wst = GF_OK;
+        if (defer_t1) {           /* the initial thread alone: publish and go on */
+            h->payload_bytes = 0;
+            h->t_publish = now_ns();
+            st_rel_sys64(&h->seq, t + 1);
+            S->pend_ticket1 = t + 1;
+            S->pend_fmt_key = ship ? key : 0;
+            *defer_t1 = t + 1;
+            ret = 0;
+            continue;
+        }
         if (lane == leader) {
             h->payload_bytes = 0;   /* the host walks records by their own sizes */
             h->t_publish = now_ns();
@@ -365,6 +441,40 @@ template <class... A> __device__ inline int64_t rpc(uint32_t op, const char *fmt
     return rpc_issue(op, fmt, a, status);
 }
 
+/* the result of a deferred call, by its ticket + 1 (initial thread only) */
+static __device__ __noinline__ int64_t deferred_value(unsigned long long t1)
+{
+    gf_state *S = s_st;
+    if (S->pend_ticket1 == t1)
+        rpc_collect_deferred(S);
+    return S->done_ticket1 == t1 ? S->done_val : -1;
+}
+} // namespace gfd
+
+/* Result of a printf-family call.  Converting it to int gives the call's
+ * return value (waiting for the host if the call was deferred); a program
+ * that ignores it never waits for the call.  Use it in the statement that
+ * made the call: a deferred result read after two or more later RPCs of the
+ * initial thread reads -1. */
+struct gf_call_result {
+    int64_t v;
+    unsigned long long t1;     /* ticket + 1 of a deferred call; 0: v is the result */
+    __device__ operator int() const { return (int)(t1 ? gfd::deferred_value(t1) : v); }
+};
+
+namespace gfd {
+template <class... A> __device__ inline gf_call_result rpc_deferrable(uint32_t op, const char *fmt, A... args)
+{
+    argpack a;
+    pack_all(a, args...);
+    if (is_initial_thread()) {
+        unsigned long long t1 = 0;
+        const int64_t r = rpc_issue(op, fmt, a, nullptr, &t1);
+        return gf_call_result{t1 ? 0 : r, t1};
+    }
+    return gf_call_result{rpc_issue(op, fmt, a, nullptr), 0ull};
+}
+
 /* the kernel split: the host launches this region as its own kernel and
  * answers with the kernel's grid (declared next to run_region) */
 static __device__ int64_t split_launch(gf_state *S, int *status)
@@ -379,6 +489,10 @@ static __device__ __noinline__ int rpc_post1(uint32_t op, const argpack &a, unsi
     gf_state *S = s_st;
     if (a.bytes() > S->slot_bytes - GF_SLOT_PAYLOAD_OFF)
         return GF_EINVAL;
+    if (S->pend_ticket1)
+        rpc_collect_deferred(S);
+    if (*(volatile int32_t *)&S->error)
+        return S->error;
     const unsigned long long t = atomicAdd(&S->rpc_ticket, 1ull);
     uint8_t *slot = (uint8_t *)(S->ring_slots + (t % S->nslots) * (uint64_t)S->slot_bytes);
     gf_slot_hdr *h = (gf_slot_hdr *)slot;
@@ -551,13 +665,13 @@ static __device__ __noinline__ size_t fread_bulk(void *buf, size_t size, size_t 
 /* ====================================================================== libc over RPC */
 /* printf family: formatted on the host by the real libc, one landing pad per
  * argument-type signature (paper Fig. 4b), records grouped per warp. */
-template <class... A> __device__ inline int gf_printf(const char *fmt, A... args)
+template <class... A> __device__ inline gf_call_result gf_printf(const char *fmt, A... args)
 {
-    return (int)gfd::rpc(GF_OP_PRINTF, fmt, nullptr, (unsigned long long)GF_STDOUT_H, args...);
+    return gfd::rpc_deferrable(GF_OP_PRINTF, fmt, (unsigned long long)GF_STDOUT_H, args...);
 }
-template <class... A> __device__ inline int gf_fprintf(GF_FILE f, const char *fmt, A... args)
+template <class... A> __device__ inline gf_call_result gf_fprintf(GF_FILE f, const char *fmt, A... args)
 {
-    return (int)gfd::rpc(GF_OP_PRINTF, fmt, nullptr, (unsigned long long)f, args...);
+    return gfd::rpc_deferrable(GF_OP_PRINTF, fmt, (unsigned long long)f, args...);
 }
 __device__ inline GF_FILE gf_stdout() { return GF_STDOUT_H; }
 __device__ inline GF_FILE gf_stderr() { return GF_STDERR_H; }
@@ -613,7 +727,50 @@ __device__ inline const char *gf_getenv(const char *name)
 {
     return (const char *)gfd::rpc(GF_OP_GETENV, nullptr, nullptr, name);
 }
-/* generic RPC to a landing pad registered with gf_rpc_register */
+/* Generic RPC to a landing pad registered with gf_rpc_register (paper
+ * Sec. 3.2, Fig. 4): `nargs` (<= GF_MAX_ARGS) arguments described by gf_arg
+ * (gf_layout.h), integers sign- or zero-extended to 64 bits in `word`.
+ * *ret (may be NULL) receives the landing pad's return value, -1 on failure.
+ * Returns GF_OK, GF_EINVAL (bad tag, count or offset, or a record larger
+ * than a ring slot), GF_ERING, GF_ETIMEDOUT, or the program's first error.
+ * The lanes of a warp that call it with the same opcode and argument tags
+ * share one ring slot. */
+__device__ inline int gf_rpc(uint32_t opcode, const gf_arg *args, int nargs, int64_t *ret)
+{
+    if (ret)
+        *ret = -1;
+    if (nargs < 0 || nargs > GF_MAX_ARGS || (nargs > 0 && !args))
+        return GF_EINVAL;
+    gfd::argpack a;
+    for (int k = 0; k < nargs; k++) {
+        const gf_arg &g = args[k];
+        switch (g.tag) {
+        case GF_T_I32: case GF_T_U32: case GF_T_I64: case GF_T_U64: case GF_T_F64: case GF_T_PTR:
+            a.val(g.tag, g.word);
+            break;
+        case GF_T_STR:
+            if (g.ptr)
+                a.blob(GF_T_STR, g.ptr, gf_strlen((const char *)g.ptr) + 1u);
+            else
+                a.val(GF_T_PTR, 0);
+            break;
+        case GF_T_BLOB_R: case GF_T_BLOB_W: case GF_T_BLOB_RW:
+            if (!g.ptr || g.off >= 65536u || g.off > g.bytes)
+                return GF_EINVAL;
+            a.blob(g.tag, g.ptr, g.bytes, g.off);
+            break;
+        default:
+            return GF_EINVAL;
+        }
+    }
+    int st = GF_OK;
+    const int64_t r = gfd::rpc_issue(opcode, nullptr, a, &st);
+    if (ret)
+        *ret = r;
+    return st;
+}
+/* the same call with its arguments as a C++ parameter pack (values, strings,
+ * gf_ref_read / gf_ref_write / gf_ref_readwrite, gf_ref_lookup) */
 template <class... A> __device__ inline int64_t gf_rpc(uint32_t opcode, int *status, A... args)
 {
     return gfd::rpc(opcode, nullptr, status, args...);

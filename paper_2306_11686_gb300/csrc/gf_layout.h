@@ -94,6 +94,26 @@ typedef struct gf_rec_hdr {
 
 #define GF_MAX_ARGS 16
 
+/* One argument of the array form of gf_rpc (paper Sec. 3.2, Fig. 4c: an
+ * argument is a value, or a reference to an object with a mode, a size and
+ * the pointer's offset inside the object).
+ *   value arguments   tag GF_T_I32 / U32 / I64 / U64 / F64 / PTR: the bits in
+ *                     `word` (a double as its IEEE bits); ptr, bytes, off unused;
+ *   string            tag GF_T_STR: ptr = the NUL-terminated string;
+ *   references        tag GF_T_BLOB_R / BLOB_W / BLOB_RW: ptr = start of the
+ *                     underlying object, bytes = its size (it travels inside
+ *                     the ring slot), off = the argument pointer's offset in
+ *                     it (< 65536); write and readwrite objects are copied
+ *                     back after the host call. */
+typedef struct gf_arg {
+    uint64_t word;
+    const void *ptr;
+    uint32_t bytes;
+    uint32_t off;
+    char tag;
+    char pad[7];
+} gf_arg;
+
 /* standard stream handles (the device never sees host FILE* values for these) */
 #define GF_STDOUT_H 1ull
 #define GF_STDERR_H 2ull
@@ -175,6 +195,11 @@ typedef struct gf_state {
     uint32_t split;            /* 1: regions run as host-launched kernels (the paper's split) */
     /* results written by the device */
     int32_t exit_code, error, main_done;
+    /* the initial thread's deferred call (printf family, result not yet
+     * needed): ticket + 1, 0 = none; the last one collected and its result */
+    uint64_t pend_ticket1, pend_fmt_key;
+    uint64_t done_ticket1;
+    int64_t done_val;
     uint64_t st_calls[GF_NSTAT];  /* RPC calls per opcode (lane records)              */
     uint64_t st_slots[GF_NSTAT];  /* ring slots per opcode                            */
     uint64_t st_wait_ns;          /* device ns spent waiting for the host             */

@@ -53,13 +53,15 @@ GF_MAIN(fwrite_modes)(int argc, char **argv)
 }
 
 /*
- * fig4_probe opcode               buffer 0 = int64 out[8]
+ * fig4_probe opcode [array]       buffer 0 = int64 out[8]
  * The call site of the paper's worked example (Fig. 4),
  *     r = fscanf(fd, "%f %i %i", &s.f, s.a ? &i : &s.b, p);
  * issued to a user landing pad: fd by value (an opaque FILE*), the format as a
  * read-only reference, &s.f readwrite with the whole struct at offset
  * offsetof(f), &i write-only (s.a != 0), and p -- an interior pointer no
  * analysis pins down -- looked up in the device heap at run time.
+ * With "array" the same call goes through the array form of gf_rpc, the
+ * arguments described one by one in gf_arg records.
  */
 struct fig4_S {
     int a, b;
@@ -88,7 +90,42 @@ GF_MAIN(fig4_probe)(int argc, char **argv)
     const unsigned long long fd = 0xF11E0ull;
     int st = 0;
     long long r;
-    if (s.a)
+    if (argc > 2 && argv[2][0] == 'a') {
+        gf_arg args[5];
+        memset(args, 0, sizeof args);
+        args[0].tag = GF_T_PTR;                       /* the FILE*, by value */
+        args[0].word = fd;
+        args[1].tag = GF_T_BLOB_R;                    /* the format, read only */
+        args[1].ptr = fmt;
+        args[1].bytes = 9;
+        args[2].tag = GF_T_BLOB_RW;                   /* &s.f: the whole struct, readwrite */
+        args[2].ptr = &s;
+        args[2].bytes = sizeof(fig4_S);
+        args[2].off = offsetof(fig4_S, f);
+        if (s.a) {                                    /* &i: write only */
+            args[3].tag = GF_T_BLOB_W;
+            args[3].ptr = &i;
+            args[3].bytes = sizeof(int);
+        } else {
+            args[3].tag = GF_T_BLOB_RW;
+            args[3].ptr = &s;
+            args[3].bytes = sizeof(fig4_S);
+            args[3].off = offsetof(fig4_S, b);
+        }
+        uint64_t base = 0, size = 0;                  /* p: its object found at run time */
+        if (gf_find_obj(p, &base, &size)) {
+            args[4].tag = GF_T_BLOB_RW;
+            args[4].ptr = (const void *)base;
+            args[4].bytes = (uint32_t)size;
+            args[4].off = (uint32_t)((uint64_t)p - base);
+        } else {
+            args[4].tag = GF_T_PTR;
+            args[4].word = (uint64_t)p;
+        }
+        int64_t r64 = 0;
+        st = gf_rpc(op, args, 5, &r64);
+        r = r64;
+    } else if (s.a)
         r = gf_rpc(op, &st, fd, gf_ref_read(fmt, 9, 0), gf_ref_readwrite(&s, sizeof(fig4_S), offsetof(fig4_S, f)),
                    gf_ref_write(&i, sizeof(int), 0), gf_ref_lookup(p));
     else

@@ -142,6 +142,8 @@ _sig = {
     "gf_mlp_topk": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(gf_synth_loop),
                                    ctypes.POINTER(gf_shape), ctypes.c_int, ctypes.c_uint32, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int)]),
+    "gf_fp64_add_rate": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_double)]),
     "gf_axpy_batch_graph": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P,
                                            ctypes.POINTER(ctypes.c_float)]),
 }

@@ -55,6 +55,32 @@ def _timed_run(ctx, stream, name, argv, bufs):
     return e0.elapsed_time(e1) / 1e3
 
 
+def printf_rate(T=1 << 20, out_dir=None, server_threads=4):
+    """The printf-only half of the stress program (T iterations x 4 printf,
+    mixed int/double formats) with warp aggregation on and off: calls/s, the
+    device round-trip p50/p99 and the lane records per ring slot."""
+    import torch
+    tmp = tempfile.mkdtemp(prefix="gfprintf", dir=out_dir)
+    stream = torch.cuda.Stream()
+    out = {}
+    for agg in (1, 0):
+        with gf.Context(aggregate=agg, stream=stream, heap_bytes=64 << 20, server_threads=server_threads,
+                        stdout_path=os.path.join(tmp, "out.txt"), timeout_ns=int(120e9)) as ctx:
+            _timed_run(ctx, stream, "printf_only", [1 << 14], [])          # warm-up
+            t = _timed_run(ctx, stream, "printf_only", [T], [])
+            st = ctx.stats()
+            calls = int(st.rpc_calls[gf.OP_PRINTF])
+            if calls != 4 * T:
+                raise RuntimeError(f"printf_only: {calls} calls served, {4 * T} issued")
+            out["aggregated" if agg else "per_thread"] = {
+                "calls_per_s": round(4 * T / t), "seconds": round(t, 4), "rpc_p50_ns": st.rpc_p50_ns,
+                "rpc_p99_ns": st.rpc_p99_ns, "records_per_slot": round(calls / max(1, int(st.rpc_slots[gf.OP_PRINTF])), 2)}
+    shutil.rmtree(tmp, ignore_errors=True)
+    out["aggregation_speedup"] = round(out["aggregated"]["calls_per_s"] / out["per_thread"]["calls_per_s"], 2)
+    out["workload"] = f"{T} iterations x 4 printf, host server {server_threads} threads"
+    return out
+
+
 def stress(args):
     import torch
     T = 1 << 20
@@ -258,20 +284,22 @@ def link(args):
     print(json.dumps(line))
 
 
-def hbm(args):
-    """One large legacy loop through the plain runtime (one static chunk-1
-    parallel region, z = a x + y, 24 B per iteration) at N = 2^26 and 2^28:
-    inputs far larger than L2, so the region's GB/s is HBM bandwidth."""
-    import torch
-    peak = None
+def _hbm_peak():
     try:
         with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")) as f:
-            peak = float(json.load(f)["hbm_gbs"])
+            return float(json.load(f)["hbm_gbs"])
     except Exception:
-        pass
+        return None
+
+
+def axpy_regions(logs, reps=5):
+    """One axpy loop z = 2.5 x + y through the plain runtime (one static
+    chunk-1 parallel region, 24 B per iteration) at N = 2^k for k in logs;
+    the best of `reps` region times.  Checked against torch's own axpy."""
+    import torch
     res = {}
     stream = torch.cuda.Stream()
-    for lg in ((args.hbm_log2,) if getattr(args, "hbm_log2", None) else (26, 28)):
+    for lg in logs:
         n = 1 << lg
         x = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1, 1)
         y = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1, 1)
@@ -283,7 +311,7 @@ def hbm(args):
         with gf.Context(stream=stream, heap_bytes=64 << 20, timeout_ns=int(60e9)) as ctx:
             _timed_run(ctx, stream, "loops", [0, 1, 1, 0], bufs)
             ts = []
-            for _ in range(5):
+            for _ in range(reps):
                 _timed_run(ctx, stream, "loops", [0, 1, 1, 0], bufs)
                 st = ctx.stats()
                 ts.append(st.region_ns / max(1, st.regions) / 1e9)
@@ -291,6 +319,14 @@ def hbm(args):
         t = min(ts)
         res[f"2^{lg}"] = {"region_s": t, "GBps": 24 * n / t / 1e9, "bytes": 24 * n, "correct": ok}
         del x, y, z
+    return res
+
+
+def hbm(args):
+    """One large legacy loop through the plain runtime at N = 2^26 and 2^28:
+    inputs far larger than L2, so the region's GB/s is HBM bandwidth."""
+    peak = _hbm_peak()
+    res = axpy_regions((args.hbm_log2,) if getattr(args, "hbm_log2", None) else (26, 28))
     best = max(v["GBps"] for v in res.values())
     line = {"metric": "loop GB/s (% HBM peak)", "value": round(best, 1), "unit": "GB/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",

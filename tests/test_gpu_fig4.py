@@ -26,7 +26,9 @@ def golden_rows():
     return rows
 
 
-def test_fig4_argument_kinds_and_copy_back(gf_lib):
+@pytest.mark.parametrize("form", ["variadic", "array"])
+def test_fig4_argument_kinds_and_copy_back(gf_lib, form):
+    """Both call forms of gf_rpc: the parameter pack and the gf_arg array."""
     import torch
     gf = gf_lib
     seen = []
@@ -51,7 +53,7 @@ def test_fig4_argument_kinds_and_copy_back(gf_lib):
     out = torch.zeros(8, dtype=torch.int64, device="cuda")
     with gf.Context(timeout_ns=10_000_000_000, heap_bytes=64 << 20) as c:
         assert gf.gf_rpc_register(c.h, 300, cb, None) == 0
-        rc, ec = c.run("fig4_probe", [300], [(out, 1)])
+        rc, ec = c.run("fig4_probe", [300] + (["array"] if form == "array" else []), [(out, 1)])
     assert ec == 0
     got, fmt = seen[0], seen[1]
     for k, kind, tag, nbytes, off in golden_rows():
