@@ -51,14 +51,15 @@ typedef int32_t gf_program;            /* registry id from gf_program_lookup    
 
 /* Runtime configuration.  Fill with gf_config_default, then override. */
 typedef struct gf_config {
-    uint64_t heap_bytes;          /* device heap arena per program instance (default 4 GiB)        */
+    uint64_t heap_bytes;          /* default heap quota of a program (default 4 GiB)               */
     uint32_t heap_small_pct;      /* percent of the arena for the small-size slabs (default 50)    */
-    uint32_t ring_slots;          /* ring slots per program instance, power of two (default 4096)  */
+    uint32_t ring_slots;          /* default ring-slot quota of a program, power of two (4096)     */
     uint32_t slot_bytes;          /* bytes per slot, multiple of 64, >= 1024 (default 4096)        */
     uint32_t aggregate;           /* 1 = warp-aggregated RPC, 0 = one slot per calling thread      */
     uint32_t server_threads;      /* host RPC server threads started by gf_init (default 1;
                                      0 = the caller serves with gf_rpc_serve / gf_wait)            */
-    uint32_t max_programs;        /* program instances that may run at once (default 1)           */
+    uint32_t max_programs;        /* program instances that may run at once (default 1): each has
+                                     its state, reduction partials, format cache and bulk arena  */
     uint32_t grid;                /* blocks per program launch, 0 = SMs x occupancy / max_programs */
     int64_t timeout_ns;           /* bound of every device wait (default 30 s)                     */
     void *stream;                 /* cudaStream_t for gf_run_main (NULL = a stream of the context) */
@@ -77,7 +78,22 @@ typedef struct gf_config {
                                      under a profiler that serialises kernels (ncu): the program
                                      then times out waiting for it. */
     uint32_t pad0;
+    uint64_t heap_pool_bytes;     /* device heap shared by all running programs: a launch takes its
+                                     heap quota from it (0 = heap_bytes x max_programs)           */
+    uint32_t ring_pool_slots;     /* ring slots shared by all running programs: a launch takes its
+                                     ring quota from it (0 = ring_slots x max_programs)           */
+    uint32_t pad1;
 } gf_config;
+
+/* Memory a launch asks for (gf_launch_q).  Zero fields take the context's
+ * defaults (gf_config.heap_bytes, gf_config.ring_slots).  The heap quota is
+ * rounded up to 256 KiB and split like a whole arena (heap_small_pct); the
+ * ring quota is a power of two, at least the number of server threads. */
+typedef struct gf_quota {
+    uint64_t heap_bytes;
+    uint32_t ring_slots;
+    uint32_t pad;
+} gf_quota;
 
 /* A buffer mapped into the program before main (the loader's job, paper
  * Sec. 3.1).  Device pointers are used in place.  Host pointers are copied to
@@ -123,6 +139,10 @@ typedef struct gf_stats {
     uint64_t copy_ns;             /* their device time (included in region_ns)             */
     uint64_t host_ring_bytes;     /* ring bytes the host served: records written by the device,
                                      8-byte returns read back (cumulative)                  */
+    uint64_t t_start_ns, t_end_ns;/* device %globaltimer at main's entry and return (one clock
+                                     for all programs on the device: intervals can be compared) */
+    uint64_t heap_quota;          /* heap bytes the program was admitted with              */
+    uint64_t ring_quota;          /* ring slots the program was admitted with              */
 } gf_stats;
 
 /* Host landing pad for a user opcode (>= 256).  `rec` points at the lane
@@ -170,10 +190,21 @@ GF_API int gf_run_main(gf_ctx *ctx, gf_program prog, int argc, const char *const
 
 /* Asynchronous launch for serving and batching: like gf_run_main up to the
  * kernel launch, on `stream` (NULL = cfg.stream) with `grid` blocks (0 = the
- * configured share).  *h receives the handle.  GF_EBUSY when no instance is
- * free (admission by ring and heap capacity). */
+ * configured share), with the default heap and ring quotas.  *h receives the
+ * handle.  GF_EBUSY when the program cannot be admitted now. */
 GF_API int gf_launch(gf_ctx *ctx, gf_program prog, int argc, const char *const *argv,
                      const gf_buf *bufs, int nbufs, void *stream, uint32_t grid, gf_handle **h);
+
+/* gf_launch with explicit quotas (q may be NULL = defaults).  Admission by
+ * ring and heap memory: the program starts only when a free instance, its
+ * heap quota (from the context's heap pool) and its ring quota (from the ring
+ * pool) are all available; otherwise nothing is taken and GF_EBUSY returns,
+ * and the caller retries after a running program has been collected with
+ * gf_wait.  GF_EINVAL when a quota exceeds its whole pool (it could never be
+ * admitted) or the ring quota is not a power of two. */
+GF_API int gf_launch_q(gf_ctx *ctx, gf_program prog, int argc, const char *const *argv,
+                       const gf_buf *bufs, int nbufs, void *stream, uint32_t grid, const gf_quota *q,
+                       gf_handle **h);
 
 /* 1 if the program behind h has finished (its kernel completed), else 0. */
 GF_API int gf_done(gf_handle *h);

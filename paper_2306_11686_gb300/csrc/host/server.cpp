@@ -586,8 +586,16 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
 
 int Server::poll(Segment &seg, uint32_t tid, uint32_t nthr)
 {
-    if (!seg.active.load(std::memory_order_acquire))
-        return 0;
+    /* announce this poller before looking at `active`: whoever clears
+     * `active` and then sees no pollers knows nobody reads the segment */
+    seg.pollers.fetch_add(1, std::memory_order_seq_cst);
+    const int n = seg.active.load(std::memory_order_seq_cst) ? poll_active(seg, tid, nthr) : 0;
+    seg.pollers.fetch_sub(1, std::memory_order_release);
+    return n;
+}
+
+int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
+{
     const uint32_t N = seg.nslots;
     int served = 0;
     uint32_t gap = 0;

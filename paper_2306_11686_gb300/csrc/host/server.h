@@ -41,6 +41,10 @@ struct Segment {
     uint8_t *bulk = nullptr;        /* host address of the bulk arena (large fwrite/fread) */
     uint64_t bulk_bytes = 0;
     std::atomic<bool> active{false};
+    /* server threads inside poll() for this segment; the runtime waits for
+     * zero after clearing `active` before it hands the slots to another
+     * program */
+    std::atomic<int> pollers{0};
     /* scan state: each slot is served for its own next ticket, so a claimant
      * that never publishes blocks only its slot, not the ring */
     std::vector<uint64_t> expect;   /* next ticket each slot will carry               */
@@ -103,6 +107,7 @@ class Server {
     int64_t call(uint32_t opcode, const char *fmt, const uint8_t *rec, Segment *seg = nullptr);
 
   private:
+    int poll_active(Segment &seg, uint32_t tid, uint32_t nthreads);
     int64_t do_printf(const char *fmt, const uint8_t *rec, std::string &out, uint64_t *stream);
     FILE *file_of(uint64_t h);
     void emit(uint64_t stream, const std::string &s);

@@ -93,7 +93,7 @@ GF_MAIN(fig4_probe)(int argc, char **argv)
     if (argc > 2 && argv[2][0] == 'a') {
         gf_arg args[5];
         memset(args, 0, sizeof args);
-        args[0].tag = GF_T_PTR;                       /* the FILE*, by value */
+        args[0].tag = GF_T_U64;                       /* the FILE*, by value (as its 64 bits) */
         args[0].word = fd;
         args[1].tag = GF_T_BLOB_R;                    /* the format, read only */
         args[1].ptr = fmt;

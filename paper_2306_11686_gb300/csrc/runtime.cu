@@ -11,9 +11,11 @@
  *  - bulk fwrite/fread payloads move by copy-engine DMA on a separate stream,
  *    double-buffered through pinned staging, while the program's grid keeps
  *    running (no SM time spent copying);
- *  - each program instance owns a ring segment, a heap arena and its state, so
- *    concurrent programs (serving) are isolated and admission is a matter of a
- *    free instance.
+ *  - the context holds one device heap pool and one ring pool; a launch takes
+ *    a program instance (its state and staging) plus a heap quota and a
+ *    ring-slot quota carved from the pools, so concurrent programs (serving)
+ *    are isolated, and a program is admitted only when an instance, its heap
+ *    quota and its ring quota are all free (otherwise GF_EBUSY).
  */
 #include <cuda_runtime.h>
 #include <stdio.h>
@@ -22,6 +24,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <chrono>
 #include <condition_variable>
 #include <mutex>
@@ -69,6 +72,52 @@ extern "C" __attribute__((visibility("default"))) int gf_program_register(const 
 }
 
 /* ------------------------------------------------------------------ context */
+/* First-fit allocator of unit ranges in [0, total): the heap pool in 256 KiB
+ * slabs, the ring pool in slots.  Callers hold the context's admission lock. */
+struct RangeAlloc {
+    uint64_t total = 0;
+    std::map<uint64_t, uint64_t> free_;   /* start -> length, disjoint, not touching */
+    void init(uint64_t n)
+    {
+        total = n;
+        free_.clear();
+        if (n)
+            free_[0] = n;
+    }
+    bool alloc(uint64_t n, uint64_t *out)
+    {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n)
+                continue;
+            const uint64_t a = it->first, l = it->second;
+            free_.erase(it);
+            if (l > n)
+                free_[a + n] = l - n;
+            *out = a;
+            return true;
+        }
+        return false;
+    }
+    void release(uint64_t a, uint64_t n)
+    {
+        if (!n)
+            return;
+        auto it = free_.emplace(a, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && a + n == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
 struct Staged {
     void *host;
     void *dev;
@@ -95,10 +144,12 @@ struct Instance {
     gf_state *d_state = nullptr;
     void *d_partials = nullptr;
     void *d_fmt = nullptr;
-    uint8_t *d_heap = nullptr;
+    uint8_t *d_heap = nullptr;      /* this launch's heap quota inside the context's pool */
     void *d_meta = nullptr, *d_heads = nullptr, *d_cur = nullptr, *d_ext = nullptr, *d_lsize = nullptr;
     uint32_t nslabs = 0, npages = 0;
     uint64_t slab_bytes = 0, large_bytes = 0;
+    uint64_t heap_first = 0, heap_units = 0;    /* quota in the heap pool, in slabs */
+    uint64_t ring_first = 0, ring_n = 0;        /* quota in the ring pool, in slots */
     char *d_argv = nullptr;
     uint8_t *bulk_host = nullptr;   /* pinned, device-mapped bulk arena */
     uint64_t bulk_dev = 0;
@@ -129,6 +180,11 @@ struct gf_ctx {
     uint8_t *ring_host = nullptr;
     uint64_t ring_dev = 0;
     size_t ring_bytes = 0;
+    uint8_t *heap_pool = nullptr;   /* device heap shared out as per-launch quotas */
+    uint64_t heap_pool_bytes = 0;
+    uint64_t max_slabs = 0, max_pages = 0;
+    RangeAlloc heap_ra, ring_ra;
+    std::mutex adm_mu;              /* admission: instances, heap and ring quotas */
     std::vector<Instance *> inst;
     gfh::Server server;
     std::vector<std::thread> threads;
@@ -183,6 +239,9 @@ extern "C" GF_API void gf_config_default(gf_config *c)
     c->split_regions = 0;
     c->pad0 = 0;
     c->device = -1;
+    c->heap_pool_bytes = 0;
+    c->ring_pool_slots = 0;
+    c->pad1 = 0;
 }
 
 extern "C" GF_API const char *gf_strerror(int e)
@@ -310,26 +369,18 @@ static int inst_alloc(gf_ctx *c, Instance *in)
     GF_CK(cudaMalloc(&in->d_partials, (size_t)c->nsm * GF_MAX_BLOCKS_PER_SM * 16));
     GF_CK(cudaMalloc(&in->d_fmt, (size_t)cf.fmt_cache * 8));
     GF_CK(cudaMalloc((void **)&in->d_argv, GF_ARGV_BYTES));
-    /* heap arena: [small slabs | large pages] */
-    const uint64_t slab = 1ull << GF_SLAB_SHIFT, page = 1ull << GF_PAGE_SHIFT;
-    in->slab_bytes = (cf.heap_bytes * cf.heap_small_pct / 100) / slab * slab;
-    in->large_bytes = (cf.heap_bytes - in->slab_bytes) / page * page;
-    in->nslabs = (uint32_t)(in->slab_bytes / slab);
-    in->npages = (uint32_t)(in->large_bytes / page);
-    if (in->slab_bytes + in->large_bytes)
-        GF_CK(cudaMalloc((void **)&in->d_heap, in->slab_bytes + in->large_bytes));
-    GF_CK(cudaMalloc(&in->d_meta, (size_t)std::max<uint32_t>(in->nslabs, 1) * 16));
+    /* heap metadata, sized for the largest quota (the whole pool); the heap
+     * itself is the launch's quota inside the context's pool */
+    GF_CK(cudaMalloc(&in->d_meta, (size_t)std::max<uint64_t>(c->max_slabs, 1) * 16));
     GF_CK(cudaMalloc(&in->d_heads, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * GF_HEAP_LANES * 8));
     GF_CK(cudaMalloc(&in->d_cur, (size_t)GF_MAX_SM * GF_HEAP_NCLASS * 4));
     GF_CK(cudaMalloc(&in->d_ext, (size_t)GF_LARGE_EXT_MAX * 8));
-    GF_CK(cudaMalloc(&in->d_lsize, (size_t)std::max<uint32_t>(in->npages, 1) * 4));
+    GF_CK(cudaMalloc(&in->d_lsize, (size_t)std::max<uint64_t>(c->max_pages, 1) * 4));
     GF_CK(cudaEventCreateWithFlags(&in->ev_done, cudaEventDisableTiming));
     if (cf.split_regions)
         GF_CK(cudaStreamCreateWithFlags(&in->region_stream, cudaStreamNonBlocking));
-    in->seg.nslots = cf.ring_slots;
     in->seg.slot_bytes = cf.slot_bytes;
     in->seg.prog = (uint32_t)in->idx;
-    in->seg.slots = c->ring_host + (size_t)in->idx * cf.ring_slots * cf.slot_bytes;
     if (cf.bulk_bytes) {
         if (cudaHostAlloc((void **)&in->bulk_host, cf.bulk_bytes, cudaHostAllocMapped | cudaHostAllocPortable) !=
             cudaSuccess)
@@ -351,7 +402,6 @@ static void inst_free(Instance *in)
     cudaFree(in->d_argv);
     if (in->bulk_host)
         cudaFreeHost(in->bulk_host);
-    cudaFree(in->d_heap);
     cudaFree(in->d_meta);
     cudaFree(in->d_heads);
     cudaFree(in->d_cur);
@@ -383,6 +433,8 @@ extern "C" GF_API int gf_finalize(gf_ctx *c)
     }
     if (c->ring_host)
         cudaFreeHost(c->ring_host);
+    if (c->heap_pool)
+        cudaFree(c->heap_pool);
     if (c->intern_host)
         cudaFreeHost(c->intern_host);
     for (DmaLane &L : c->dma) {
@@ -416,6 +468,10 @@ extern "C" GF_API int gf_init(const gf_config *cfg, gf_ctx **out)
         return GF_EINVAL;
     if (cf.server_threads && (!pow2(cf.server_threads) || cf.server_threads > cf.ring_slots))
         return GF_EINVAL;
+    const uint64_t ring_pool = cf.ring_pool_slots ? cf.ring_pool_slots : (uint64_t)cf.ring_slots * cf.max_programs;
+    const uint64_t heap_pool = cf.heap_pool_bytes ? cf.heap_pool_bytes : cf.heap_bytes * cf.max_programs;
+    if (ring_pool < cf.ring_slots || heap_pool < cf.heap_bytes || ring_pool > (1ull << 24))
+        return GF_EINVAL;
     if (cf.split_regions > 1 || (cf.split_regions && cf.server_threads == 0))
         return GF_EINVAL;                /* the split needs a server thread to launch regions */
     gf_ctx *c = new gf_ctx();
@@ -439,8 +495,20 @@ extern "C" GF_API int gf_init(const gf_config *cfg, gf_ctx **out)
     cudaDeviceGetLimit(&stack, cudaLimitStackSize);
     if (stack < 4096)
         cudaDeviceSetLimit(cudaLimitStackSize, 4096);
+    /* heap pool: one device allocation, shared out as per-launch quotas in
+     * whole slabs; per-instance metadata is sized for a quota of the whole pool */
+    {
+        const uint64_t slab = 1ull << GF_SLAB_SHIFT, page = 1ull << GF_PAGE_SHIFT;
+        c->heap_pool_bytes = heap_pool / slab * slab;
+        c->max_slabs = c->heap_pool_bytes / slab;
+        c->max_pages = c->heap_pool_bytes / page;
+        c->heap_ra.init(c->max_slabs);
+        if (c->heap_pool_bytes && cudaMalloc((void **)&c->heap_pool, c->heap_pool_bytes) != cudaSuccess)
+            return fail(GF_ENOMEM);
+    }
+    c->ring_ra.init(ring_pool);
     /* ring: pinned, device-mapped host memory */
-    c->ring_bytes = (size_t)cf.ring_slots * cf.slot_bytes * cf.max_programs;
+    c->ring_bytes = (size_t)ring_pool * cf.slot_bytes;
     if (cudaHostAlloc((void **)&c->ring_host, c->ring_bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
         return fail(GF_ENOMEM);
     memset(c->ring_host, 0, c->ring_bytes);
@@ -570,8 +638,80 @@ static void release_staged(gf_handle *h, bool copy_back)
 
 static int inst_start(gf_ctx *c, Instance *in, cudaStream_t stream, uint32_t grid);
 
+/* Admission: a free instance, a heap quota and a ring quota, all or none.
+ * GF_EINVAL for a quota no pool can ever hold, GF_EBUSY when it does not fit
+ * now.  The heap quota is [small slabs | large pages] like a whole arena. */
+static int admit(gf_ctx *c, const gf_quota *q, Instance **out)
+{
+    const gf_config &cf = c->cfg;
+    const uint64_t slab = 1ull << GF_SLAB_SHIFT, page = 1ull << GF_PAGE_SHIFT;
+    const uint64_t hb = q && q->heap_bytes ? q->heap_bytes : cf.heap_bytes;
+    const uint64_t rs = q && q->ring_slots ? q->ring_slots : cf.ring_slots;
+    const uint64_t hu = (hb + slab - 1) / slab;
+    if (!pow2(rs) || rs > c->ring_ra.total || rs < std::max<uint32_t>(1, cf.server_threads) ||
+        hu > c->heap_ra.total)
+        return GF_EINVAL;
+    std::lock_guard<std::mutex> g(c->adm_mu);
+    Instance *in = nullptr;
+    for (Instance *x : c->inst)
+        if (!x->busy.load()) {
+            in = x;
+            break;
+        }
+    if (!in)
+        return GF_EBUSY;
+    uint64_t ho = 0, ro = 0;
+    if (hu && !c->heap_ra.alloc(hu, &ho))
+        return GF_EBUSY;
+    if (!c->ring_ra.alloc(rs, &ro)) {
+        c->heap_ra.release(ho, hu);
+        return GF_EBUSY;
+    }
+    in->busy = true;
+    in->heap_first = ho;
+    in->heap_units = hu;
+    in->ring_first = ro;
+    in->ring_n = rs;
+    const uint64_t bytes = hu * slab;
+    in->d_heap = hu ? c->heap_pool + ho * slab : nullptr;
+    in->slab_bytes = (bytes * cf.heap_small_pct / 100) / slab * slab;
+    in->large_bytes = (bytes - in->slab_bytes) / page * page;
+    in->nslabs = (uint32_t)(in->slab_bytes / slab);
+    in->npages = (uint32_t)(in->large_bytes / page);
+    in->seg.slots = c->ring_host + ro * cf.slot_bytes;
+    in->seg.nslots = (uint32_t)rs;
+    *out = in;
+    return GF_OK;
+}
+
+/* Stop serving the instance's ring segment and wait until no server thread
+ * is inside it, so its slots can go to another program. */
+static void seg_stop(gf_ctx *c, Instance *in)
+{
+    if (in->seg.active.exchange(false))
+        c->nactive--;
+    while (in->seg.pollers.load() != 0)
+        std::this_thread::yield();
+}
+
+/* Give the instance and its quotas back (the program has ended or never started). */
+static void inst_release(gf_ctx *c, Instance *in)
+{
+    std::lock_guard<std::mutex> g(c->adm_mu);
+    c->heap_ra.release(in->heap_first, in->heap_units);
+    c->ring_ra.release(in->ring_first, in->ring_n);
+    in->heap_units = in->ring_n = 0;
+    in->busy = false;
+}
+
 extern "C" GF_API int gf_launch(gf_ctx *c, gf_program prog, int argc, const char *const *argv, const gf_buf *bufs,
                                 int nbufs, void *stream, uint32_t grid, gf_handle **out)
+{
+    return gf_launch_q(c, prog, argc, argv, bufs, nbufs, stream, grid, nullptr, out);
+}
+
+extern "C" GF_API int gf_launch_q(gf_ctx *c, gf_program prog, int argc, const char *const *argv, const gf_buf *bufs,
+                                  int nbufs, void *stream, uint32_t grid, const gf_quota *quota, gf_handle **out)
 {
     if (!c || !out || argc < 0 || nbufs < 0 || nbufs > GF_MAX_BUFS || (nbufs && !bufs) || (argc && !argv))
         return GF_EINVAL;
@@ -609,17 +749,10 @@ extern "C" GF_API int gf_launch(gf_ctx *c, gf_program prog, int argc, const char
         need += strlen(argv[k]) + 1;
     if (need > GF_ARGV_BYTES)
         return GF_EINVAL;
-    /* admission: a free instance (its ring segment and heap arena) */
+    /* admission: a free instance, its heap quota and its ring quota */
     Instance *in = nullptr;
-    for (Instance *x : c->inst) {
-        bool f = false;
-        if (x->busy.compare_exchange_strong(f, true)) {
-            in = x;
-            break;
-        }
-    }
-    if (!in)
-        return GF_EBUSY;
+    if ((rc = admit(c, quota, &in)) != GF_OK)
+        return rc;
     gf_handle *h = new gf_handle();
     h->ctx = c;
     h->inst = in;
@@ -630,7 +763,8 @@ extern "C" GF_API int gf_launch(gf_ctx *c, gf_program prog, int argc, const char
     in->region_grid = region_grid;
     auto bail = [&](int e) {
         release_staged(h, false);
-        in->busy = false;
+        seg_stop(c, in);
+        inst_release(c, in);
         delete h;
         return e;
     };
@@ -680,8 +814,6 @@ extern "C" GF_API int gf_launch(gf_ctx *c, gf_program prog, int argc, const char
     cudaError_t le = pe.launch(args, grid, GF_BLOCK_THREADS, h->stream);
     if (le != cudaSuccess || cudaEventRecord(in->ev_done, h->stream) != cudaSuccess) {
         fprintf(stderr, "gf: launch of %s failed: %s\n", pe.name.c_str(), cudaGetErrorString(le));
-        in->seg.active = false;
-        c->nactive--;
         return bail(GF_ECUDA);
     }
     *out = h;
@@ -698,8 +830,8 @@ static int inst_start(gf_ctx *c, Instance *in, cudaStream_t stream, uint32_t gri
     s.nworkers = grid * GF_BLOCK_THREADS - 32;
     s.aggregate = c->cfg.aggregate;
     s.timeout_ns = c->cfg.timeout_ns;
-    s.ring_slots = c->ring_dev + (uint64_t)in->idx * c->cfg.ring_slots * c->cfg.slot_bytes;
-    s.nslots = c->cfg.ring_slots;
+    s.ring_slots = c->ring_dev + in->ring_first * c->cfg.slot_bytes;
+    s.nslots = (uint32_t)in->ring_n;
     s.slot_bytes = c->cfg.slot_bytes;
     s.fmt_cache = (uint64_t)in->d_fmt;
     s.fmt_cache_cap = c->cfg.fmt_cache;
@@ -751,30 +883,26 @@ static int inst_start(gf_ctx *c, Instance *in, cudaStream_t stream, uint32_t gri
  * state, or nullptr when every instance is taken. */
 gf_state *gf_inst_acquire(gf_ctx *c, void *stream, uint32_t nblocks, int *idx)
 {
-    for (Instance *x : c->inst) {
-        bool f = false;
-        if (x->busy.compare_exchange_strong(f, true)) {
-            memset(&x->h_init, 0, sizeof x->h_init);
-            cudaStream_t s = (cudaStream_t)(stream ? stream : c->own_stream);
-            if (inst_start(c, x, s, nblocks ? nblocks : 1) != GF_OK || cudaStreamSynchronize(s) != cudaSuccess) {
-                x->seg.active = false;
-                x->busy = false;
-                return nullptr;
-            }
-            *idx = x->idx;
-            return x->d_state;
-        }
+    Instance *x = nullptr;
+    if (admit(c, nullptr, &x) != GF_OK)
+        return nullptr;
+    memset(&x->h_init, 0, sizeof x->h_init);
+    cudaStream_t s = (cudaStream_t)(stream ? stream : c->own_stream);
+    if (inst_start(c, x, s, nblocks ? nblocks : 1) != GF_OK || cudaStreamSynchronize(s) != cudaSuccess) {
+        seg_stop(c, x);
+        inst_release(c, x);
+        return nullptr;
     }
-    return nullptr;
+    *idx = x->idx;
+    return x->d_state;
 }
 
 /* The caller has drained its stream: stop serving the segment, free the instance. */
 void gf_inst_release(gf_ctx *c, int idx)
 {
     Instance *in = c->inst[(size_t)idx];
-    if (in->seg.active.exchange(false))
-        c->nactive--;
-    in->busy = false;
+    seg_stop(c, in);
+    inst_release(c, in);
 }
 
 int gf_ctx_server_threads(gf_ctx *c) { return (int)c->cfg.server_threads; }
@@ -829,10 +957,9 @@ extern "C" GF_API int gf_wait(gf_handle *h, int *exit_code, int64_t timeout_ns)
             break;
         if (q != cudaErrorNotReady) {
             fprintf(stderr, "gf: program failed: %s\n", cudaGetErrorString(q));
-            in->seg.active = false;
-            c->nactive--;
+            seg_stop(c, in);
             release_staged(h, false);
-            in->busy = false;
+            inst_release(c, in);
             delete h;
             return GF_ECUDA;
         }
@@ -845,8 +972,7 @@ extern "C" GF_API int gf_wait(gf_handle *h, int *exit_code, int64_t timeout_ns)
                 timeout_ns)
             return GF_ETIMEDOUT;
     }
-    in->seg.active.store(false, std::memory_order_release);
-    c->nactive--;
+    seg_stop(c, in);
     int rc = GF_OK;
     if (cudaMemcpyAsync(&in->h_final, in->d_state, sizeof(gf_state), cudaMemcpyDeviceToHost, h->stream) !=
             cudaSuccess ||
@@ -886,6 +1012,10 @@ extern "C" GF_API int gf_wait(gf_handle *h, int *exit_code, int64_t timeout_ns)
         st.copy_regions = f.st_copy_regions;
         st.copy_ns = f.st_copy_ns;
         st.host_ring_bytes = c->server.stats.ring_bytes;
+        st.t_start_ns = f.t_main_start;
+        st.t_end_ns = f.t_main_end;
+        st.heap_quota = in->heap_units << GF_SLAB_SHIFT;
+        st.ring_quota = in->ring_n;
     }
     if (rc == GF_OK && in->h_final.error)
         rc = in->h_final.error;
@@ -893,7 +1023,7 @@ extern "C" GF_API int gf_wait(gf_handle *h, int *exit_code, int64_t timeout_ns)
         *exit_code = in->h_final.exit_code;
     if (c->out)
         fflush(c->out);
-    in->busy = false;
+    inst_release(c, in);
     delete h;
     return rc;
 }

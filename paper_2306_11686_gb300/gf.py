@@ -42,7 +42,14 @@ class gf_config(ctypes.Structure):
         ("bulk_bytes", ctypes.c_uint64),
         ("split_regions", ctypes.c_uint32),
         ("pad0", ctypes.c_uint32),
+        ("heap_pool_bytes", ctypes.c_uint64),
+        ("ring_pool_slots", ctypes.c_uint32),
+        ("pad1", ctypes.c_uint32),
     ]
+
+
+class gf_quota(ctypes.Structure):
+    _fields_ = [("heap_bytes", ctypes.c_uint64), ("ring_slots", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 class gf_buf(ctypes.Structure):
@@ -78,6 +85,10 @@ class gf_stats(ctypes.Structure):
         ("copy_regions", ctypes.c_uint64),
         ("copy_ns", ctypes.c_uint64),
         ("host_ring_bytes", ctypes.c_uint64),
+        ("t_start_ns", ctypes.c_uint64),
+        ("t_end_ns", ctypes.c_uint64),
+        ("heap_quota", ctypes.c_uint64),
+        ("ring_quota", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -116,6 +127,9 @@ _sig = {
                                    ctypes.POINTER(gf_buf), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gf_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                  ctypes.POINTER(gf_buf), ctypes.c_int, _P, ctypes.c_uint32, ctypes.POINTER(_P)]),
+    "gf_launch_q": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                   ctypes.POINTER(gf_buf), ctypes.c_int, _P, ctypes.c_uint32, ctypes.POINTER(gf_quota),
+                                   ctypes.POINTER(_P)]),
     "gf_done": (ctypes.c_int, [_P]),
     "gf_wait": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int64]),
     "gf_rpc_serve": (ctypes.c_int, [_P, ctypes.POINTER(gf_serve_opts)]),
@@ -225,13 +239,16 @@ class Context:
             _check(rc, f"gf_run_main({name})")
         return rc, ec.value
 
-    def launch(self, name, argv, bufs=(), stream=None, grid=0):
+    def launch(self, name, argv, bufs=(), stream=None, grid=0, heap_bytes=0, ring_slots=0):
+        """gf_launch_q with the given quotas (0 = the context's defaults);
+        returns (rc, handle)."""
         pid = self.program(name)
         av, keep = make_argv([name] + [str(a) for a in argv])
         b = make_bufs(bufs)
         h = _P()
         s = stream.cuda_stream if stream is not None and not isinstance(stream, int) else stream
-        rc = gf_launch(self.h, pid, len(keep), av, b, len(bufs), s, grid, ctypes.byref(h))
+        q = gf_quota(heap_bytes, ring_slots, 0)
+        rc = gf_launch_q(self.h, pid, len(keep), av, b, len(bufs), s, grid, ctypes.byref(q), ctypes.byref(h))
         return rc, h
 
     def wait(self, h, timeout_ns=0):
