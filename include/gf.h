@@ -79,7 +79,8 @@ typedef struct gf_config {
                                      then times out waiting for it. */
     uint32_t pad0;
     uint64_t heap_pool_bytes;     /* device heap shared by all running programs: a launch takes its
-                                     heap quota from it (0 = heap_bytes x max_programs)           */
+                                     heap quota from it (0 = heap_bytes x max_programs; both
+                                     rounded up to whole 256 KiB slabs)                          */
     uint32_t ring_pool_slots;     /* ring slots shared by all running programs: a launch takes its
                                      ring quota from it (0 = ring_slots x max_programs)           */
     uint32_t pad1;

@@ -468,9 +468,14 @@ extern "C" GF_API int gf_init(const gf_config *cfg, gf_ctx **out)
         return GF_EINVAL;
     if (cf.server_threads && (!pow2(cf.server_threads) || cf.server_threads > cf.ring_slots))
         return GF_EINVAL;
+    /* pools: whole slabs; a quota is rounded up to whole slabs, so the
+     * default pool holds max_programs default quotas exactly */
+    const uint64_t slab_b = 1ull << GF_SLAB_SHIFT;
+    const uint64_t quota0 = (cf.heap_bytes + slab_b - 1) / slab_b * slab_b;
     const uint64_t ring_pool = cf.ring_pool_slots ? cf.ring_pool_slots : (uint64_t)cf.ring_slots * cf.max_programs;
-    const uint64_t heap_pool = cf.heap_pool_bytes ? cf.heap_pool_bytes : cf.heap_bytes * cf.max_programs;
-    if (ring_pool < cf.ring_slots || heap_pool < cf.heap_bytes || ring_pool > (1ull << 24))
+    const uint64_t heap_pool =
+        (cf.heap_pool_bytes ? (cf.heap_pool_bytes + slab_b - 1) / slab_b * slab_b : quota0 * cf.max_programs);
+    if (ring_pool < cf.ring_slots || heap_pool < quota0 || ring_pool > (1ull << 24))
         return GF_EINVAL;
     if (cf.split_regions > 1 || (cf.split_regions && cf.server_threads == 0))
         return GF_EINVAL;                /* the split needs a server thread to launch regions */
@@ -499,7 +504,7 @@ extern "C" GF_API int gf_init(const gf_config *cfg, gf_ctx **out)
      * whole slabs; per-instance metadata is sized for a quota of the whole pool */
     {
         const uint64_t slab = 1ull << GF_SLAB_SHIFT, page = 1ull << GF_PAGE_SHIFT;
-        c->heap_pool_bytes = heap_pool / slab * slab;
+        c->heap_pool_bytes = heap_pool;
         c->max_slabs = c->heap_pool_bytes / slab;
         c->max_pages = c->heap_pool_bytes / page;
         c->heap_ra.init(c->max_slabs);
