@@ -11,7 +11,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "_build")
-SOURCES = ["axpy_sum", "jacobi", "exact_sum", "stress", "spmv_serve", "loops", "synth"]
+SOURCES = ["axpy_sum", "jacobi", "exact_sum", "stress", "spmv_serve", "loops", "loops_rpc", "synth"]
 CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-Wall", "-Wno-unknown-pragmas"]
 
 

@@ -207,6 +207,33 @@ def test_loops_oracle_elementwise_and_untouched(oracle_bin, tmp_path):
     assert got.tolist() == [1.0, 3.0, 5.0, -1.0, -1.0, -1.5, -2.0, -2.5, -3.0]
 
 
+def test_loops_rpc_oracle_lines_and_values(oracle_bin, tmp_path):
+    """Loops whose bodies print and use a heap block every 4096 iterations:
+    an empty loop prints nothing, a 1-iteration loop prints its i = 0, a loop of
+    8193 prints i = 0, 4096, 8192 (and not 8193), each line carrying the
+    loop index, the iteration and the value the element receives."""
+    trips = np.array([0, 1, 8193], dtype=np.int64)
+    off = np.array([0, 1, 2], dtype=np.int64)
+    a = np.array([3.0, -0.5, 0.25])
+    total = 2 + 8193 + 1                                  # the last element belongs to no loop
+    x = np.arange(total, dtype=np.float64)
+    y = np.full(total, 0.1)
+    z = np.full(total, 7.0)
+    for name, arr in [("t", trips), ("a", a), ("o", off), ("x", x), ("y", y), ("z", z)]:
+        inputs.write_raw(tmp_path / f"{name}.bin", arr)
+    out = run([oracle_bin("loops_rpc"), "3", tmp_path / "t.bin", tmp_path / "a.bin", tmp_path / "o.bin",
+               tmp_path / "x.bin", tmp_path / "y.bin", tmp_path / "z.bin", tmp_path / "zo.bin", str(total)])
+    got = np.fromfile(tmp_path / "zo.bin")
+    # loop 1: element 1 = -0.5 * 1 + 0.1; loop 2: element 2 + i = 0.25 * (2 + i) + 0.1
+    want = z.copy()
+    want[1] = -0.5 * 1.0 + 0.1
+    i = np.arange(8193)
+    want[2 + i] = 0.25 * (2.0 + i) + 0.1               # exact product, one rounding of the add: as in C
+    assert got.tolist() == want.tolist()
+    assert out.splitlines() == ["1 0 %.17g" % want[1], "2 0 %.17g" % want[2], "2 4096 %.17g" % want[2 + 4096],
+                                "2 8192 %.17g" % want[2 + 8192]]
+
+
 # ------------------------------------------------------------------ synth
 
 def _f32(v):
