@@ -237,6 +237,9 @@ def main():
     ap.add_argument("--int-adds", type=int, default=None,
                     help="how many of the five neighbour adds run on the integer pipe (0..5; the program's "
                          "default when omitted)")
+    ap.add_argument("--kseg", type=int, default=None,
+                    help="run each sweep as columns of K planes per parallel iteration (0 = one iteration per "
+                         "point; the program's default when omitted)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the same-process extra measurements (printf calls/s with and without warp "
@@ -280,8 +283,10 @@ def main():
     ctx = gf.Context(stream=stream, heap_bytes=heap, heap_small_pct=5,
                      stdout_path=os.path.join(tmp, f"stdout_r{rank}.txt"), **ckw)
     argv = [N, sweeps, "-" if args.no_write else out_path]
-    if args.int_adds is not None:
-        argv.append(args.int_adds)
+    if args.int_adds is not None or args.kseg is not None:
+        argv.append(1 if args.int_adds is None else args.int_adds)
+    if args.kseg is not None:
+        argv.append(args.kseg)
 
     def step(buf):
         rc, ec = ctx.run("jacobi", argv, [(buf, gf.GF_BUF_IN)])

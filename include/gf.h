@@ -256,6 +256,26 @@ GF_API int gf_axpy_batch_graph(int n, const int64_t *trips, const double *a, con
                                const double *y, double *z, const uint32_t *grid, const uint32_t *block, int reps,
                                void *stream, float *ms);
 
+/* The graph form of loops that call libc (the loops_rpc program's body):
+ * loop k computes z[off_k + i] = a_k * x[off_k + i] + y[off_k + i] for
+ * i < trips[k], and every 4096th iteration passes the value through a device
+ * heap block of 64 << (k % 8) bytes and prints "k i value" by RPC.  One CUDA
+ * graph with one kernel node per loop, each with grid[k] x block[k] threads
+ * (either array may be NULL: 256 threads, enough blocks to cover the loop up
+ * to 8 per SM; block a multiple of 32, <= 256: the device heap's per-block
+ * hand-off area holds 8 warps).  A program instance of ctx
+ * (its heap quota and ring; answered by the context's server threads, at
+ * least one) is borrowed for the call.  `warmup` untimed replays, then `reps`
+ * timed ones on `stream`; *ms (may be NULL) = mean ms per timed replay.
+ * Every replay prints its lines again.  x, y, z and fails (uint64 count of
+ * heap blocks not granted or corrupted) are device memory; trips, a, off,
+ * grid, block are host arrays of n entries.  Errors: GF_EINVAL, GF_EBUSY,
+ * GF_ECUDA, or a device error of the loops' calls. */
+GF_API int gf_loops_rpc_graph(gf_ctx *ctx, int n, const int64_t *trips, const double *a, const int64_t *off,
+                              const double *x, const double *y, double *z, unsigned long long *fails,
+                              const uint32_t *grid, const uint32_t *block, int warmup, int reps, void *stream,
+                              float *ms);
+
 /* ------------------------------------------------------------------ launch-shape tuning */
 
 /* A synthetic legacy loop (the learned-model workload): per iteration it reads

@@ -92,13 +92,79 @@ __device__ int jacobi_sweep(const double *u, double *un, uint32_t nn, uint64_t c
 }
 
 /*
- * jacobi n sweeps out_path [int_adds]   buffers: 0 = input grid (n^3 doubles, i fastest)
+ * The same sweep written with the k loop inside the parallel loop: work item
+ * t is the column (i, j) over planes [k0, k0 + kseg), t = (k0 / kseg) * n^2 +
+ * j * n + i, so consecutive items are consecutive i (coalesced).  Walking up
+ * the column, the k - 1 and k neighbours of a point are the values loaded for
+ * the previous point, so each point loads five values instead of seven, and
+ * the index split and boundary test are paid once per column segment.  Every
+ * point's arithmetic and its order are those of jacobi_sweep, so the grid
+ * and the residual are the same bits.
+ */
+template <int INT_ADDS>
+__device__ int jacobi_sweep_col(const double *u, double *un, uint32_t nn, uint32_t kseg, double *res)
+{
+    const uint32_t sk = nn * nn;
+    const uint32_t nseg = (nn + kseg - 1) / kseg;
+    const gf_udiv32 dn = gf_udiv32::make(nn), dsk = gf_udiv32::make(sk);
+    return gf_reduce<double, GF_RED_MAX>(
+        0, (int64_t)nseg * sk, GF_SCHED_STATIC, 1,
+        [=](int64_t t64) -> double {
+            const uint32_t t = (uint32_t)t64;
+            const uint32_t seg = dsk.div(t), ij = t - seg * sk;
+            const uint32_t j = dn.div(ij), im1 = ij - 1u - j * nn;
+            const uint32_t k0 = seg * kseg, k1 = min(k0 + kseg, nn);
+            double *o = un + ij;
+            if (max(im1, j - 1u) >= nn - 2u) {            /* a boundary column */
+                for (uint32_t k = k0; k < k1; k++)
+                    o[(size_t)k * sk] = 0.0;
+                return 0.0;
+            }
+            const double *c = u + ij;
+            uint32_t k = k0;
+            if (k == 0) {                                  /* the bottom boundary plane */
+                o[0] = 0.0;
+                k = 1;
+            }
+            const uint32_t kend = min(k1, nn - 1u);
+            long long best = 0;                            /* bits of the largest |un - u|, +0 to start */
+            if (k < kend) {
+                double um = __ldg(c + (size_t)(k - 1) * sk), u0 = __ldg(c + (size_t)k * sk);
+                for (; k < kend; k++) {
+                    const double *p = c + (size_t)k * sk;
+                    const double up = __ldg(p + sk);
+                    const double nb[6] = {__ldg(p - 1), __ldg(p + 1), __ldg(p - nn), __ldg(p + nn), um, up};
+                    double v = nb[0];
+#pragma unroll
+                    for (int q = 1; q < 6; q++)
+                        v = q <= INT_ADDS ? gf_dadd_int(v, nb[q]) : __dadd_rn(v, nb[q]);
+                    v = gf_div6_int(v);
+                    o[(size_t)k * sk] = v;
+                    /* |un - u| >= 0: its bits order as the values do; NaN is skipped, as the reduction does */
+                    const long long b = __double_as_longlong(gf_fabs_int(__dadd_rn(v, -u0)));
+                    if (b <= 0x7ff0000000000000ll && b > best)
+                        best = b;
+                    um = u0;
+                    u0 = up;
+                }
+            }
+            if (k1 == nn && nn > 1)                        /* the top boundary plane */
+                o[(size_t)(nn - 1) * sk] = 0.0;
+            return __longlong_as_double(best);
+        },
+        res);
+}
+
+/*
+ * jacobi n sweeps out_path [int_adds [kseg]]   buffers: 0 = input grid (n^3 doubles, i fastest)
  *
  * Laplace Jacobi sweeps with the six-neighbour average, boundary written as 0,
  * a fresh grid from the device heap every sweep (old one freed after the
  * swap), the max residual over the interior fused into the sweep as a max
  * reduction, one printf per sweep, the final grid fwrite'd.  int_adds (0..5,
- * default 1) is how many of the five neighbour adds run on the integer pipe.
+ * default 1) is how many of the five neighbour adds run on the integer pipe;
+ * kseg (default 0) > 0 runs the sweep as columns of kseg planes
+ * (jacobi_sweep_col) instead of one parallel iteration per point.
  * Compiled for 4 resident blocks per SM (64 registers): the sweep waits on
  * L2 more than on any pipe, and more warps hide that latency.
  */
@@ -109,9 +175,11 @@ GF_MAIN_BOUNDS(jacobi, 4)(int argc, char **argv)
     const long long n = gf_atoll(argv[1]);
     const int sweeps = (int)gf_atoll(argv[2]);
     const int int_adds = argc > 4 ? (int)gf_atoll(argv[4]) : 1;
+    const long long kseg = argc > 5 ? gf_atoll(argv[5]) : 0;
     const double *u0 = (const double *)gf_buffer(0);
     const uint64_t cells = (uint64_t)n * n * n;
-    if (n < 1 || n > 1290 || !u0 || gf_buffer_bytes(0) < cells * 8 || int_adds < 0 || int_adds > 5)
+    if (n < 1 || n > 1290 || !u0 || gf_buffer_bytes(0) < cells * 8 || int_adds < 0 || int_adds > 5 || kseg < 0 ||
+        kseg > n)
         return 2;
     const uint32_t nn = (uint32_t)n;
     const double *u = u0;
@@ -124,13 +192,25 @@ GF_MAIN_BOUNDS(jacobi, 4)(int argc, char **argv)
         }
         double res = 0.0;
         int rc;
-        switch (int_adds) {
-        case 0: rc = jacobi_sweep<0>(u, un, nn, cells, &res); break;
-        case 1: rc = jacobi_sweep<1>(u, un, nn, cells, &res); break;
-        case 2: rc = jacobi_sweep<2>(u, un, nn, cells, &res); break;
-        case 3: rc = jacobi_sweep<3>(u, un, nn, cells, &res); break;
-        case 4: rc = jacobi_sweep<4>(u, un, nn, cells, &res); break;
-        default: rc = jacobi_sweep<5>(u, un, nn, cells, &res); break;
+        if (kseg > 0) {
+            const uint32_t ks = (uint32_t)kseg;
+            switch (int_adds) {
+            case 0: rc = jacobi_sweep_col<0>(u, un, nn, ks, &res); break;
+            case 1: rc = jacobi_sweep_col<1>(u, un, nn, ks, &res); break;
+            case 2: rc = jacobi_sweep_col<2>(u, un, nn, ks, &res); break;
+            case 3: rc = jacobi_sweep_col<3>(u, un, nn, ks, &res); break;
+            case 4: rc = jacobi_sweep_col<4>(u, un, nn, ks, &res); break;
+            default: rc = jacobi_sweep_col<5>(u, un, nn, ks, &res); break;
+            }
+        } else {
+            switch (int_adds) {
+            case 0: rc = jacobi_sweep<0>(u, un, nn, cells, &res); break;
+            case 1: rc = jacobi_sweep<1>(u, un, nn, cells, &res); break;
+            case 2: rc = jacobi_sweep<2>(u, un, nn, cells, &res); break;
+            case 3: rc = jacobi_sweep<3>(u, un, nn, cells, &res); break;
+            case 4: rc = jacobi_sweep<4>(u, un, nn, cells, &res); break;
+            default: rc = jacobi_sweep<5>(u, un, nn, cells, &res); break;
+            }
         }
         if (rc)
             return 10;

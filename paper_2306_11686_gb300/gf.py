@@ -158,6 +158,8 @@ _sig = {
                                    ctypes.POINTER(ctypes.c_int)]),
     "gf_fp64_add_rate": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_double)]),
+    "gf_loops_rpc_graph": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int,
+                                          ctypes.c_int, _P, ctypes.POINTER(ctypes.c_float)]),
     "gf_axpy_batch_graph": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P,
                                            ctypes.POINTER(ctypes.c_float)]),
 }

@@ -44,6 +44,82 @@ def shapes(sms: int):
     return out
 
 
+# ---------------------------------------------------------------- batched loops
+BATCH_CHUNKS = (1024, 4096, 16384, 65536)
+GRAPH_BLOCKS = (128, 256)
+GRAPH_GRID_MULT = (1, 2, 4, 8)
+
+
+def tune_batch(ctx, bufs, n, reps=3, stream=None, chunks=BATCH_CHUNKS, scheds=SCHEDS):
+    """The autotuner for a batched region of `n` loops (program loops_rpc,
+    mode 1): every (chunk, schedule) candidate is timed `reps` times after a
+    warm-up (CUDA events around the whole program); returns the fastest
+    (chunk, sched) and the table {"chunk/sched": best seconds}."""
+    import torch
+    s = stream or torch.cuda.current_stream()
+    table = {}
+    for c in chunks:
+        for sc in scheds:
+            argv = [1, n, c, sc]
+            ts = []
+            for r in range(reps + 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                rc, ec = ctx.run("loops_rpc", argv, bufs)
+                e1.record(s)
+                torch.cuda.synchronize()
+                if ec != 0:
+                    raise RuntimeError(f"loops_rpc exit code {ec}")
+                if r:
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+            table[f"{c}/{sc}"] = min(ts)
+    best = min(table, key=table.get)
+    c, sc = best.split("/")
+    return (int(c), int(sc)), table
+
+
+def graph_candidates(trip, sms):
+    """Launch shapes tried for one loop of the graph form: 128 or 256 threads,
+    1 to 8 blocks per SM, never more blocks than the loop has iterations
+    for, plus the one-pass cover of the loop."""
+    out = set()
+    for b in GRAPH_BLOCKS:
+        cover = max(1, -(-trip // b))
+        out.add((min(cover, 8 * sms), b))
+        for m in GRAPH_GRID_MULT:
+            out.add((max(1, min(m * sms, cover)), b))
+    return sorted(out)
+
+
+def tune_graph(ctx, trips, a, off, x, y, z, fails, sms, reps=2, stream=None):
+    """The autotuner for the graph form: each loop alone (a one-node graph) is
+    timed under each of its candidate shapes; returns per-loop grid and block
+    arrays (uint32) and the summed per-loop best and default times."""
+    grid = np.zeros(len(trips), dtype=np.uint32)
+    block = np.zeros(len(trips), dtype=np.uint32)
+    best_sum = default_sum = 0.0
+    P = lambda arr: ctypes.c_void_p(arr.ctypes.data)
+    for k in range(len(trips)):
+        t1, a1, o1 = trips[k:k + 1].copy(), a[k:k + 1].copy(), off[k:k + 1].copy()
+        best = None
+        for g, b in graph_candidates(int(trips[k]), sms):
+            g1, b1 = np.array([g], dtype=np.uint32), np.array([b], dtype=np.uint32)
+            ms = ctypes.c_float()
+            rc = gf.gf_loops_rpc_graph(ctx.h, 1, P(t1), P(a1), P(o1), ctypes.c_void_p(x.data_ptr()),
+                                       ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                       ctypes.c_void_p(fails.data_ptr()), P(g1), P(b1), 1, reps, stream,
+                                       ctypes.byref(ms))
+            if rc != gf.GF_OK:
+                raise gf.GFError(rc, f"gf_loops_rpc_graph(loop {k})")
+            if best is None or ms.value < best[0]:
+                best = (ms.value, g, b)
+            if b == 256 and g == min(-(-int(trips[k]) // 256), 8 * sms):
+                default_sum += ms.value
+        best_sum += best[0]
+        grid[k], block[k] = best[1], best[2]
+    return grid, block, best_sum, default_sum
+
+
 def heuristic_shape(sms: int):
     """The plain runtime's fixed choice: 4 blocks of 256 per SM, small static items."""
     return (4 * sms, 256, 64, 0)

@@ -109,11 +109,33 @@ def test_jacobi_parity(gf_lib, oracle_bin, tmp_path, n, sweeps):
     assert st.heap_live_bytes == 0
 
 
+@pytest.mark.parametrize("n,sweeps,kseg", [(1, 2, 1), (2, 2, 1), (3, 2, 2), (8, 3, 3), (18, 4, 18), (67, 5, 7),
+                                            (256, 100, 8)])
+def test_jacobi_column_parity(gf_lib, oracle_bin, tmp_path, n, sweeps, kseg):
+    """The sweep as columns of kseg planes: the serial program's residual
+    lines and grid bits, including ragged last segments and the full-size
+    benchmark grid."""
+    import torch
+    gf = gf_lib
+    g = inputs.jacobi_input(n, seed=2)
+    inputs.write_f64(tmp_path / "in.bin", g)
+    want = oracle(oracle_bin, "jacobi", n, sweeps, tmp_path / "in.bin", tmp_path / "ref.bin")
+    heap = max(64 << 20, 4 * n ** 3 * 8 + (64 << 20))
+    with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=heap, heap_small_pct=5) as ctx:
+        rc, ec = ctx.run("jacobi", [n, sweeps, tmp_path / "gpu.bin", 1, kseg],
+                         [(torch.from_numpy(g).cuda(), gf.GF_BUF_IN)])
+    assert ec == 0
+    assert sorted(open(tmp_path / "out.txt").read().splitlines()) == sorted(want.splitlines())
+    assert (tmp_path / "gpu.bin").read_bytes() == (tmp_path / "ref.bin").read_bytes()
+
+
+@pytest.mark.parametrize("kseg", [0, 3, 16])
 @pytest.mark.parametrize("int_adds", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("kind", ["unit", "signed", "tiny", "huge", "ties", "smooth"])
-def test_jacobi_parity_every_pipe_split(gf_lib, oracle_bin, tmp_path, int_adds, kind):
+def test_jacobi_parity_every_pipe_split(gf_lib, oracle_bin, tmp_path, int_adds, kind, kseg):
     """Every split of the neighbour adds between the integer and FP64 pipes
-    gives the serial program's bits: on the standard grid, on a grid of mixed
+    gives the serial program's bits, one iteration per point (kseg 0) and as
+    columns of 3 or 16 planes: on the standard grid, on a grid of mixed
     signs (opposite-sign adds take the FP64 path), on grids scaled into the
     subnormal range and up by 2^200, on a constant interior (residuals tie)
     and on a smooth grid whose residual grows along the iteration order."""
@@ -136,7 +158,7 @@ def test_jacobi_parity_every_pipe_split(gf_lib, oracle_bin, tmp_path, int_adds, 
     want = oracle(oracle_bin, "jacobi", n, sweeps, tmp_path / "in.bin", tmp_path / "ref.bin")
     with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20,
                     heap_small_pct=5) as ctx:
-        rc, ec = ctx.run("jacobi", [n, sweeps, tmp_path / "gpu.bin", int_adds],
+        rc, ec = ctx.run("jacobi", [n, sweeps, tmp_path / "gpu.bin", int_adds, kseg],
                          [(torch.from_numpy(g).cuda(), gf.GF_BUF_IN)])
     assert ec == 0
     assert sorted(open(tmp_path / "out.txt").read().splitlines()) == sorted(want.splitlines())
