@@ -147,12 +147,63 @@ def batch(args):
                                 ctypes.c_void_p(yd.data_ptr()), ctypes.c_void_p(z.data_ptr()), None, None, 5,
                                 ctypes.c_void_p(stream.cuda_stream), ctypes.byref(ms))
     res["graph"] = {"replay_s": ms.value / 1e3, "GBps": 24 * total / (ms.value / 1e3) / 1e9, "rc": rc}
+    res["with_rpc_and_heap"] = batch_rpc(trips, a, off, td, ad, od, xd, yd, total, stream, _out_dir(args))
     best = res["batched_dynamic"]["GBps_regions"]
     line = {"metric": "loop GB/s (% HBM peak)", "value": round(best, 1), "unit": "GB/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{n} axpy loops, trip log-uniform 2^10..2^22, {total} iterations, 24 B/iter"},
             "detail": res}
     print(json.dumps(line))
+
+
+def batch_rpc(trips, a, off, td, ad, od, xd, yd, total, stream, out_dir):
+    """The 256 loops with a heap block and a printf every 4096 iterations
+    (loops_rpc): one region per loop, one batched region at the fixed chunk
+    4096 / dynamic and at the autotuner's (chunk, schedule), and the graph
+    form at its default shapes and at the autotuner's per-loop shapes.  Loop
+    GB/s counts the 24 B per iteration of the loop bodies."""
+    import ctypes
+    import torch
+    from . import tune
+    n = len(trips)
+    z = torch.zeros(total, dtype=torch.float64, device="cuda")
+    fails = torch.zeros(1, dtype=torch.int64, device="cuda")
+    prefix = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    bufs = [(td, 1), (ad, 1), (od, 1), (xd, 1), (yd, 1), (z, 1), (prefix, 1), (fails, 1)]
+    out = {}
+    with gf.Context(stream=stream, heap_bytes=1 << 30, server_threads=4, timeout_ns=int(60e9),
+                    stdout_path=os.devnull) as ctx:
+        t0 = time.time()
+        (chunk, sched), table = tune.tune_batch(ctx, bufs, n, reps=3, stream=stream)
+        out["batch_tuning"] = {"choice": {"chunk": chunk, "sched": sched}, "table_s": table,
+                               "tuning_s": round(time.time() - t0, 2)}
+        for label, argv in [("regions", [0, n, 1, 0]), ("batched_fixed_4096_dynamic", [1, n, 4096, 1]),
+                            ("batched_tuned", [1, n, chunk, sched])]:
+            _timed_run(ctx, stream, "loops_rpc", argv, bufs)
+            ts = [_timed_run(ctx, stream, "loops_rpc", argv, bufs) for _ in range(3)]
+            st = ctx.stats()
+            out[label] = {"program_s": min(ts), "GBps": 24 * total / min(ts) / 1e9, "regions": int(st.regions),
+                          "printf_calls": int(st.rpc_calls[gf.OP_PRINTF]),
+                          "records_per_slot": round(int(st.rpc_calls[gf.OP_PRINTF]) /
+                                                    max(1, int(st.rpc_slots[gf.OP_PRINTF])), 2)}
+        sms = ctx.grid_info("loops_rpc")[0]
+        t0 = time.time()
+        grid, block, tuned_sum, default_sum = tune.tune_graph(ctx, trips, a, off, xd, yd, z, fails, sms, reps=2,
+                                                              stream=ctypes.c_void_p(stream.cuda_stream))
+        out["graph_tuning"] = {"per_loop_best_sum_s": tuned_sum / 1e3, "per_loop_default_sum_s": default_sum / 1e3,
+                               "tuning_s": round(time.time() - t0, 2)}
+        P = lambda arr: ctypes.c_void_p(arr.ctypes.data)
+        for label, g, b in [("graph_default", None, None), ("graph_tuned", P(grid), P(block))]:
+            ms = ctypes.c_float()
+            rc = gf.gf_loops_rpc_graph(ctx.h, n, P(trips), P(a), P(off), ctypes.c_void_p(xd.data_ptr()),
+                                       ctypes.c_void_p(yd.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                       ctypes.c_void_p(fails.data_ptr()), g, b, 1, 3,
+                                       ctypes.c_void_p(stream.cuda_stream), ctypes.byref(ms))
+            if rc != gf.GF_OK:
+                raise gf.GFError(rc, "gf_loops_rpc_graph")
+            out[label] = {"replay_s": ms.value / 1e3, "GBps": 24 * total / (ms.value / 1e3) / 1e9}
+    out["heap_fails"] = int(fails.item())
+    return out
 
 
 def learned(args):
@@ -170,7 +221,31 @@ def learned(args):
 SERVE_THREADS = 4
 
 
+def _spmv_alone(serve, n, P, tmp, fp64_peak=None):
+    """The served SpMV without its libc requests: P programs at once (16
+    instances), device time of the whole set (first start to last end)."""
+    progs = [serve.Program(p, n, 10, 64, requests=False) for p in range(P)]
+    outs = [os.path.join(tmp, f"norq{p}.bin") for p in range(P)]
+    serve.serve(progs, outs, max_concurrent=min(16, P), heap_bytes=256 << 20, ring_slots=1024,
+                server_threads=SERVE_THREADS, stdout_path=os.devnull)             # warm-up
+    for pr in progs:
+        pr.reset()
+    recs, agg = serve.serve(progs, outs, max_concurrent=min(16, P), heap_bytes=256 << 20, ring_slots=1024,
+                            server_threads=SERVE_THREADS, stdout_path=os.devnull)
+    t = agg["device_s"]
+    nbytes = sum(pr.bytes_moved() for pr in progs)
+    ops = sum(pr.fp64_ops() for pr in progs)
+    out = {"programs": P, "device_s": t, "GBps": nbytes / t / 1e9, "hbm_frac": None,
+           "fp64_Gops": ops / t / 1e9, "fp64_frac": None if not fp64_peak else ops / t / fp64_peak,
+           "errors": sum(1 for r in recs if r["rc"] or r["exit"])}
+    peak = _hbm_peak()
+    if peak:
+        out["hbm_frac"] = out["GBps"] / peak
+    return out
+
+
 def serve_run(args):
+    import ctypes
     from . import serve
     P, n = 64, 1 << 20
     os.environ.setdefault("GF_SERVE_VAR0", "zero")
@@ -193,6 +268,22 @@ def serve_run(args):
     agg["errors"] = sum(a["errors"] for a in runs)
     agg["server_threads"] = SERVE_THREADS
     agg["input_gen_s"] = t_gen
+    # the plain single-program runtime on the same GPU: the same programs one at a time
+    for pr in progs:
+        pr.reset()
+    recs1, one = serve.serve(progs, outs, max_concurrent=1, heap_bytes=1 << 30, ring_slots=1024,
+                             server_threads=SERVE_THREADS, stdout_path=os.path.join(tmp, "out1.txt"))
+    agg["single_program_runtime"] = {k: one[k] for k in ("wall_s", "calls_per_s", "rpc_p50_ns_median",
+                                                          "rpc_p99_ns_max", "latency_p50_s", "latency_p99_s")}
+    agg["single_program_runtime"]["errors"] = sum(1 for r in recs1 if r["rc"] or r["exit"])
+    del progs
+    # the SpMV alone (no libc requests): one program, then 16 at once
+    ms, adds = ctypes.c_float(), ctypes.c_double()
+    gf.gf_fp64_add_rate(0, 8192, None, ctypes.byref(ms), ctypes.byref(adds))
+    peak = adds.value / (ms.value / 1e3)
+    agg["spmv_only"] = {"one": _spmv_alone(serve, n, 1, tmp, peak), "sixteen": _spmv_alone(serve, n, 16, tmp, peak),
+                        "fp64_add_peak_Gops": peak / 1e9,
+                        "bytes_per_spmv": 16 * n * 12 + (n + 1) * 8 + 2 * n * 8}
     line = {"metric": "RPC calls/s + p99 latency", "value": round(agg["calls_per_s"]), "unit": "calls/s",
             "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "64 programs, CSR SpMV 1M rows x 16 nnz, 10 passes, Poisson libc requests, "

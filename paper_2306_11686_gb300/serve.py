@@ -27,9 +27,12 @@ from . import gf, inputs
 class Program:
     """Device buffers of one served program (CSR SpMV with libc requests)."""
 
-    def __init__(self, p, n, passes, req_per_pass, device="cuda"):
+    def __init__(self, p, n, passes, req_per_pass, device="cuda", requests=True):
+        """requests=False drops the program's libc requests: the SpMV passes alone."""
         import torch
         rowptr, col, val, x0, req = inputs.serve_program_inputs(p, n=n, passes=passes, req_per_pass=req_per_pass)
+        if not requests:
+            req = req[:0]
         self.p, self.n, self.passes, self.rpp = p, n, passes, req_per_pass
         self.nnz = len(col)
         self.nreq = len(req) // 2
@@ -54,6 +57,10 @@ class Program:
     def bytes_moved(self):
         """Algorithmic SpMV bytes: values, columns, row pointers, x gather, y write."""
         return self.passes * (self.nnz * 12 + (self.n + 1) * 8 + self.n * 8 * 2)
+
+    def fp64_ops(self):
+        """FP64 operations of the SpMV passes: a multiply and an add per nonzero."""
+        return self.passes * self.nnz * 2
 
 
 def max_overlap(recs):
@@ -146,4 +153,5 @@ def serve(programs, out_paths, max_concurrent=16, rate_hz=None, seed=7, heap_byt
                   "rpc_p99_ns_max": float(max(r["p99_ns"] for r in recs)),
                   "admission_refusals": refused,
                   "max_overlap": max_overlap(recs),
-                  "spmv_GBps": sum(p.bytes_moved() for p in programs) / wall / 1e9}
+                  "spmv_GBps": sum(p.bytes_moved() for p in programs) / wall / 1e9,
+                  "device_s": (max(r["t_end_ns"] for r in recs) - min(r["t_start_ns"] for r in recs)) / 1e9}
