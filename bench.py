@@ -426,9 +426,15 @@ def main():
                        "program_ms": {"sweeps": round((st.region_ns - st.copy_ns) / 1e6, 3),
                                       "fwrite_copy_regions": round(st.copy_ns / 1e6, 3),
                                       "rpc_waits": round(st.rpc_wait_ns / 1e6, 3),
+                                      "rpc_waits_by_call": {
+                                          "printf": round(st.rpc_wait_op_ns[gf.OP_PRINTF] / 1e6, 3),
+                                          "fwrite": round(st.rpc_wait_op_ns[gf.OP_FWRITE] / 1e6, 3),
+                                          "fopen_fclose": round((st.rpc_wait_op_ns[gf.OP_FOPEN] +
+                                                                 st.rpc_wait_op_ns[gf.OP_FCLOSE]) / 1e6, 3)},
+                                      "rpc_client": round(st.rpc_client_ns / 1e6, 3),
                                       "serial_heap": round(st.heap_ns / 1e6, 3),
-                                      "rest": round((st.main_ns - st.region_ns - st.rpc_wait_ns - st.heap_ns) / 1e6,
-                                                    3)},
+                                      "rest": round((st.main_ns - st.region_ns - st.rpc_wait_ns - st.heap_ns -
+                                                     st.rpc_client_ns) / 1e6, 3)},
                        "rpc_p50_ns": st.rpc_p50_ns, "rpc_p99_ns": st.rpc_p99_ns, "rpc_wait_ns": st.rpc_wait_ns,
                        "step_s": [round(p, 6) for p in per]},
         }

@@ -120,7 +120,8 @@ typedef struct gf_stats {
     uint64_t rpc_calls[GF_NOPS];  /* lane records per opcode (index = GF_OP_*)               */
     uint64_t rpc_slots[GF_NOPS];  /* ring slots per opcode (calls / slots = aggregation)    */
     uint64_t rpc_wait_ns;         /* device time leaders spent waiting for the host        */
-    double rpc_p50_ns;            /* device round-trip latency percentiles (claim -> done) */
+    double rpc_p50_ns;            /* device round-trip latency percentiles (claim -> done) of
+                                     calls whose caller waited (not deferred printf)        */
     double rpc_p99_ns;
     uint64_t regions;             /* parallel regions run                                   */
     uint64_t region_ns;           /* device time inside regions (publish -> all blocks done) */
@@ -144,6 +145,9 @@ typedef struct gf_stats {
                                      for all programs on the device: intervals can be compared) */
     uint64_t heap_quota;          /* heap bytes the program was admitted with              */
     uint64_t ring_quota;          /* ring slots the program was admitted with              */
+    uint64_t rpc_wait_op_ns[GF_NOPS]; /* rpc_wait_ns split by opcode                        */
+    uint64_t rpc_client_ns;       /* the initial thread's time inside RPC calls outside the
+                                     waits (packing, slot claim, publication, collection)   */
 } gf_stats;
 
 /* Host landing pad for a user opcode (>= 256).  `rec` points at the lane

@@ -234,7 +234,9 @@ static __device__ __noinline__ int rpc_collect_deferred(gf_state *S)
     S->done_val = (int64_t)ld_vol64((const uint64_t *)(slot + GF_SLOT_RET_OFF));
     S->done_ticket1 = t1;
     const uint32_t op = h->opcode;
-    S->st_wait_ns += now_ns() - t0;
+    const uint64_t waited = now_ns() - t0;
+    S->st_wait_ns += waited;
+    S->st_wait_op_ns[op < GF_NSTAT ? op : 0] += waited;
     S->st_calls[op < GF_NSTAT ? op : 0]++;
     S->st_slots[op < GF_NSTAT ? op : 0]++;
     if (S->pend_fmt_key)
@@ -257,8 +259,14 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
     gf_state *S = s_st;
     const uint32_t lane = lane_id();
     const uint32_t active = __activemask();
-    if (is_initial_thread() && S->pend_ticket1)      /* keep the initial thread's calls in order */
+    const bool initial = is_initial_thread();
+    const uint64_t t_enter = initial ? now_ns() : 0;
+    uint64_t t_waited = 0;                          /* this call's waits for the host */
+    if (initial && S->pend_ticket1) {               /* keep the initial thread's calls in order */
+        const uint64_t w0 = S->st_wait_ns;
         rpc_collect_deferred(S);
+        t_waited += S->st_wait_ns - w0;
+    }
     {
         /* fail fast after the first error; one reading for the whole group */
         const int err = __shfl_sync(active, *(volatile int32_t *)&S->error, __ffs(active) - 1);
@@ -367,7 +375,10 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
             h->prog = S->prog_id;
             h->t_issue = t_issue;
         }
-        __threadfence_system();
+        /* a lone lane's own record writes are ordered before its publishing
+         * store by that store's release; a group's other lanes need the fence */
+        if (nl > 1)
+            __threadfence_system();
         __syncwarp(grp);
         int wst = GF_OK;
         if (defer_t1) {           /* the initial thread alone: publish and go on */
@@ -391,7 +402,10 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
                     wst = GF_ETIMEDOUT;
                     break;
                 }
-            atomicAdd((unsigned long long *)&S->st_wait_ns, (unsigned long long)(now_ns() - t0));
+            const uint64_t waited = now_ns() - t0;
+            t_waited += waited;
+            atomicAdd((unsigned long long *)&S->st_wait_ns, (unsigned long long)waited);
+            atomicAdd((unsigned long long *)&S->st_wait_op_ns[op < GF_NSTAT ? op : 0], (unsigned long long)waited);
             if (wst == GF_OK) {
                 const uint64_t lat = now_ns() - t_issue;
                 uint32_t bk = (uint32_t)lat;
@@ -429,6 +443,8 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
             st_rel_sys64(&h->seq, t + S->nslots);
         }
     }
+    if (initial)
+        S->st_client_ns += now_ns() - t_enter - t_waited;
     if (status)
         *status = st;
     return ret;
@@ -534,6 +550,7 @@ static __device__ __noinline__ int64_t rpc_finish1(unsigned long long t, int *st
     const int64_t r = (int64_t)ld_vol64((const uint64_t *)(slot + GF_SLOT_RET_OFF));
     const uint32_t op = h->opcode;
     atomicAdd((unsigned long long *)&S->st_wait_ns, (unsigned long long)(now_ns() - t0));
+    atomicAdd((unsigned long long *)&S->st_wait_op_ns[op < GF_NSTAT ? op : 0], (unsigned long long)(now_ns() - t0));
     atomicAdd((unsigned long long *)&S->st_calls[op < GF_NSTAT ? op : 0], 1ull);
     atomicAdd((unsigned long long *)&S->st_slots[op < GF_NSTAT ? op : 0], 1ull);
     st_rel_sys64(&h->seq, t + S->nslots);

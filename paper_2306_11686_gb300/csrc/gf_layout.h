@@ -203,6 +203,8 @@ typedef struct gf_state {
     uint64_t st_calls[GF_NSTAT];  /* RPC calls per opcode (lane records)              */
     uint64_t st_slots[GF_NSTAT];  /* ring slots per opcode                            */
     uint64_t st_wait_ns;          /* device ns spent waiting for the host             */
+    uint64_t st_wait_op_ns[GF_NSTAT]; /* the same, per opcode                          */
+    uint64_t st_client_ns;        /* initial thread: ns inside RPC calls outside the waits */
     uint64_t st_regions;
     uint64_t st_region_ns;        /* initial thread: publish -> all blocks done       */
     uint64_t st_heap_ns;          /* initial thread: time inside gf_malloc / gf_free   */

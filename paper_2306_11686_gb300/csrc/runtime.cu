@@ -1021,6 +1021,9 @@ extern "C" GF_API int gf_wait(gf_handle *h, int *exit_code, int64_t timeout_ns)
         st.t_end_ns = f.t_main_end;
         st.heap_quota = in->heap_units << GF_SLAB_SHIFT;
         st.ring_quota = in->ring_n;
+        for (int k = 0; k < GF_NOPS && k < GF_NSTAT; k++)
+            st.rpc_wait_op_ns[k] = f.st_wait_op_ns[k];
+        st.rpc_client_ns = f.st_client_ns;
     }
     if (rc == GF_OK && in->h_final.error)
         rc = in->h_final.error;

@@ -89,6 +89,8 @@ class gf_stats(ctypes.Structure):
         ("t_end_ns", ctypes.c_uint64),
         ("heap_quota", ctypes.c_uint64),
         ("ring_quota", ctypes.c_uint64),
+        ("rpc_wait_op_ns", ctypes.c_uint64 * NOPS),
+        ("rpc_client_ns", ctypes.c_uint64),
     ]
 
     def as_dict(self):
