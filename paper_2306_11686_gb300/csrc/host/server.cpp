@@ -37,6 +37,7 @@ void Segment::reset(uint32_t nthreads)
     passes.assign(nthreads, 0);
     std::lock_guard<std::mutex> g(fmt_mu);
     fmt_cache.clear();
+    fmt_local.assign(nthreads, {});
 }
 
 RecView::RecView(const uint8_t *r) : base(r)
@@ -599,6 +600,28 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
     const uint32_t N = seg.nslots;
     int served = 0;
     uint32_t gap = 0;
+    /* counters kept per call and added to the shared ones once at the end:
+     * per-slot atomic adds from every server thread made the counters' cache
+     * lines bounce between cores */
+    uint64_t n_rec = 0, n_ns = 0, n_ring = 0, n_op[GF_NSTAT] = {};
+    /* printf text of consecutive slots to one stream is written in one go;
+     * those slots are released only after their text reached the stream, so
+     * one device thread's calls still appear in program order */
+    std::string out;
+    uint64_t out_stream = 0;
+    uint64_t *held[16];
+    uint64_t held_t[16];
+    uint32_t nheld = 0;
+    auto flush = [&]() {
+        if (!out.empty())
+            emit(out_stream, out);
+        out.clear();
+        for (uint32_t k = 0; k < nheld; k++)
+            release_store(held[k], held_t[k]);
+        nheld = 0;
+    };
+    std::unordered_map<uint64_t, const std::string *> *local =
+        tid < seg.fmt_local.size() ? &seg.fmt_local[tid] : nullptr;
     /* Claims arrive in ticket order, so the next request is usually in the
      * slot after the last one served: start there and stop after a run of
      * quiet slots; every 64th pass scans all of this thread's slots to pick
@@ -621,29 +644,45 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
         const uint32_t op = h->opcode, nl = h->nlanes;
         uint8_t *pay = slot + GF_SLOT_PAYLOAD_OFF;
         const char *fmt = nullptr;
-        std::string fmt_s;
         if (h->flags & GF_SF_FMT_INLINE) {
-            fmt = (const char *)pay;
-            fmt_s.assign(fmt, strnlen(fmt, h->fmt_len));
+            const char *inl = (const char *)pay;
+            const std::string *str;
             {
                 std::lock_guard<std::mutex> g(seg.fmt_mu);
-                seg.fmt_cache[h->fmt_key] = fmt_s;
+                str = &seg.fmt_cache.emplace(h->fmt_key, std::string(inl, strnlen(inl, h->fmt_len))).first->second;
             }
+            if (local)
+                (*local)[h->fmt_key] = str;
+            fmt = str->c_str();
             pay += (h->fmt_len + 7u) & ~7u;
         } else if (h->fmt_key) {
-            std::lock_guard<std::mutex> g(seg.fmt_mu);
-            auto it = seg.fmt_cache.find(h->fmt_key);
-            if (it != seg.fmt_cache.end())
-                fmt_s = it->second;
+            const std::string *str = nullptr;
+            if (local) {
+                auto it = local->find(h->fmt_key);
+                if (it != local->end())
+                    str = it->second;
+            }
+            if (!str) {
+                std::lock_guard<std::mutex> g(seg.fmt_mu);
+                auto it = seg.fmt_cache.find(h->fmt_key);
+                if (it != seg.fmt_cache.end()) {
+                    str = &it->second;
+                    if (local)
+                        (*local)[h->fmt_key] = str;
+                }
+            }
+            /* a key never shipped: printf answers -1 per lane (no format) */
+            fmt = str ? str->c_str() : nullptr;
         }
-        if (h->fmt_key)
-            fmt = fmt_s.c_str();
         int64_t *ret = (int64_t *)(slot + GF_SLOT_RET_OFF);
         const uint8_t *end = slot + seg.slot_bytes;
+        bool hold = false;
         if (op == GF_OP_PRINTF) {
-            /* all lanes of a slot share one format: format them into one buffer and write it once */
-            std::string out;
+            /* all lanes of a slot share one format: format them into the
+             * pending text of their stream */
+            const size_t mark = out.size();
             uint64_t stream = 0;
+            bool first = true, bad_stream = false;
             for (uint32_t l = 0; l < nl && l < 32; l++) {
                 const gf_rec_hdr *rh = (const gf_rec_hdr *)pay;
                 if (pay + sizeof(gf_rec_hdr) > end || rh->bytes < sizeof(gf_rec_hdr) || pay + rh->bytes > end) {
@@ -651,22 +690,37 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
                     continue;
                 }
                 uint64_t st = 0;
+                const size_t before = out.size();
+                if (first) {
+                    /* peek at the lane's stream before formatting into the buffer */
+                    const RecView rv(pay);
+                    st = rv.nargs ? rv.word(0) : 0;
+                    if (st != out_stream)
+                        flush();
+                    out_stream = st;
+                    stream = st;
+                    first = false;
+                }
                 ret[l] = fmt ? do_printf(fmt, pay, out, &st) : -1;
-                if (l == 0)
-                    stream = st;
-                else if (st != stream) {       /* lanes writing to different streams */
-                    emit(stream, out);
-                    out.clear();
-                    stream = st;
+                if (st != stream) {                    /* lanes writing to different streams */
+                    const std::string tail = out.substr(before);
+                    out.resize(before);
+                    flush();
+                    out = tail;
+                    out_stream = stream = st;
                 }
                 pay += rh->bytes;
             }
-            if (!file_of(stream))
+            if (!first && !file_of(stream)) {
+                bad_stream = true;
+                out.resize(std::min(out.size(), mark));
+            }
+            if (bad_stream)
                 for (uint32_t l = 0; l < nl && l < 32; l++)
                     ret[l] = -1;
-            else
-                emit(stream, out);
+            hold = true;
         } else {
+            flush();                                   /* earlier text first: other calls may touch the same files */
             for (uint32_t l = 0; l < nl && l < 32; l++) {
                 const gf_rec_hdr *rh = (const gf_rec_hdr *)pay;
                 if (pay + sizeof(gf_rec_hdr) > end || rh->bytes < sizeof(gf_rec_hdr) || pay + rh->bytes > end) {
@@ -679,15 +733,31 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
         }
         const uint64_t dt = now_ns() - t0;
         h->t_host_ns = dt;
-        stats.slots++;
-        stats.records += nl;
-        stats.ns += dt;
-        stats.ring_bytes += (uint64_t)(pay - slot) + 8ull * nl;
-        stats.per_op[op < GF_NSTAT ? op : 0] += nl;
+        served++;
+        n_rec += nl;
+        n_ns += dt;
+        n_ring += (uint64_t)(pay - slot) + 8ull * nl;
+        n_op[op < GF_NSTAT ? op : 0] += nl;
         seg.expect[s] = t + N;
         seg.cursor[tid] = (s + nthr) % N;
-        release_store(&h->seq, t + 2);
-        served++;
+        if (hold) {
+            held[nheld] = &h->seq;
+            held_t[nheld] = t + 2;
+            if (++nheld == 16 || out.size() >= (16u << 10))
+                flush();
+        } else {
+            release_store(&h->seq, t + 2);
+        }
+    }
+    flush();
+    if (served) {
+        stats.slots += (uint64_t)served;
+        stats.records += n_rec;
+        stats.ns += n_ns;
+        stats.ring_bytes += n_ring;
+        for (int k = 0; k < GF_NSTAT; k++)
+            if (n_op[k])
+                stats.per_op[k] += n_op[k];
     }
     return served;
 }

@@ -50,8 +50,11 @@ struct Segment {
     std::vector<uint64_t> expect;   /* next ticket each slot will carry               */
     std::vector<uint32_t> cursor;   /* per server thread: slot to start the next scan */
     std::vector<uint32_t> passes;   /* per server thread: scans so far                */
-    std::unordered_map<uint64_t, std::string> fmt_cache;   /* fmt_key -> format */
+    std::unordered_map<uint64_t, std::string> fmt_cache;   /* fmt_key -> format (never overwritten) */
     std::mutex fmt_mu;
+    /* per server thread: fmt_key -> the string in fmt_cache, so a thread
+     * takes the shared lock only for a format it has not seen */
+    std::vector<std::unordered_map<uint64_t, const std::string *>> fmt_local;
     void reset(uint32_t nthreads);
 };
 

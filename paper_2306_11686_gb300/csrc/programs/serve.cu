@@ -55,6 +55,8 @@ GF_MAIN_BOUNDS(spmv_serve, 4)(int argc, char **argv)
         return 10;
     double *x = xb, *y = yb;
     long long q0 = 0;
+    /* paired loads need 16-byte aligned values and 8-byte aligned columns */
+    const bool vec = ((uintptr_t)val & 15u) == 0 && ((uintptr_t)col & 7u) == 0;
     for (int r = 0; r < R; r++) {
         long long q1 = q0;
         while (q1 < nreq && (req[2 * q1] >> 32) == r)
@@ -70,11 +72,31 @@ GF_MAIN_BOUNDS(spmv_serve, 4)(int argc, char **argv)
             return 10;
         const int rc = gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) {
             double s = 0.0;
-            /* unrolled: the loads of eight nonzeros are in flight together (the
-             * adds stay in CSR order, one rounding each, as in the serial program) */
+            const long long j0 = __ldg(rowptr + i), j1 = __ldg(rowptr + i + 1);
+            long long j = j0;
+            /* the adds stay in CSR order, one rounding each, as in the serial
+             * program; values and columns of a row are read two at a time
+             * (16-byte and 8-byte loads from an even index), and the gathers
+             * of eight nonzeros are in flight together.  The matrix is
+             * constant for the whole program (read-only loads); x was written
+             * by the previous pass, so it takes ordinary loads */
+            if (vec) {
+                if ((j & 1) && j < j1) {
+                    s = s + __ldg(val + j) * xs[__ldg(col + j)];
+                    j++;
+                }
+#pragma unroll 4
+                for (; j + 1 < j1; j += 2) {
+                    const double2 v = __ldg((const double2 *)(val + j));
+                    const int2 c = __ldg((const int2 *)(col + j));
+                    const double x0 = xs[c.x], x1 = xs[c.y];
+                    s = s + v.x * x0;
+                    s = s + v.y * x1;
+                }
+            }
 #pragma unroll 8
-            for (long long j = rowptr[i]; j < rowptr[i + 1]; j++)
-                s = s + val[j] * xs[col[j]];
+            for (; j < j1; j++)
+                s = s + __ldg(val + j) * xs[__ldg(col + j)];
             ys[i] = s;
             if (qa == qb || !((mark[i >> 5] >> (i & 31)) & 1u))
                 return;

@@ -89,8 +89,13 @@ def test_axpy_host_buffers_e2e(gf_lib, oracle_bin, tmp_path):
     assert np.array_equal(yh, np.fromfile(tmp_path / "ref.bin"))
 
 
-@pytest.mark.parametrize("n,sweeps", [(1, 2), (2, 2), (3, 2), (8, 3), (18, 4), (67, 5), (256, 100)])
+@pytest.mark.parametrize("n,sweeps", [(1, 2), (2, 2), (3, 2), (8, 3), (12, 60), (18, 4), (20, 40), (67, 5),
+                                     (256, 100)])
 def test_jacobi_parity(gf_lib, oracle_bin, tmp_path, n, sweeps):
+    """Bit-exact against the serial program.  The small grids with many
+    sweeps reuse the same few heap blocks while they fit in an SM's L1, so a
+    read of a grid through the read-only path that saw data from two sweeps
+    earlier would change the result."""
     import torch
     gf = gf_lib
     g = inputs.jacobi_input(n, seed=2)
