@@ -35,9 +35,10 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 operations of the serial program per interior point: 5 neighbour adds,
 # the division by 6, the residual's subtract.
 FP64_OPS_PER_POINT = 7
-# DRAM bytes (read + write) of one full launch from an ncu capture of the
-# current program kernel, or None when the kernel changed since the capture.
-TRAFFIC_PER_LAUNCH = None
+# DRAM bytes (read + write) of one full launch, scaled from an ncu capture of
+# the current program kernel (20 sweeps, no final write: 3.1818 + 3.0993 GB,
+# 314.05 MB per sweep) to 100 sweeps plus the final fwrite's 134.2 MB read.
+TRAFFIC_PER_LAUNCH = 100 * 314_054_050 + 134_217_728
 
 
 def fp64_pipe_ops_per_point(int_adds):
@@ -47,7 +48,7 @@ def fp64_pipe_ops_per_point(int_adds):
     return (5 - int_adds) + 1
 
 
-def fp64_add_peak(gf, stream, tries=5, iters=8192):
+def fp64_add_peak(gf, stream, tries=3, iters=512):
     """The measured FP64 add rate of this GPU (gf_fp64_add_rate: eight
     independent add chains per thread, CUDA events), best of `tries`, with the
     SM clock sampled while it runs."""
@@ -365,12 +366,13 @@ def main():
                                if peak_clocks.get("sm_mhz") else None,
                                "clocks": peak_clocks,
                                "how": "gf_fp64_add_rate: SMs x resident blocks of 256 threads, 8 independent "
-                                      "add.rn.f64 chains x 8192 per thread, CUDA events, best of 5"},
+                                      "add.rn.f64 chains x 512 per thread (2.4 ms per launch), CUDA events, "
+                                      "best of 3"},
                  "hbm": {"workload": "one axpy loop z = 2.5 x + y, N = 2^28, one static chunk-1 region "
                                      "through the plain runtime (24 B per iteration, 6.4 GB)",
                          "GBps": round(ax["GBps"], 1), "frac": round(ax["GBps"] / peak, 4),
                          "peak": peak, "peak_kind": peak_kind, "correct": ax["correct"]},
-                 "stress": measure.printf_rate(1 << 20, out_dir=out_dir)}
+                 "stress": measure.printf_rate(1 << 20, out_dir=out_dir, server_threads=8)}
     cpu = cpu_omp = None
     if rank == 0 and args.cpu_sweeps > 0:
         cv, cdt, cc, pinned = cpu_oracle_sample(N, args.cpu_sweeps, tmp)
