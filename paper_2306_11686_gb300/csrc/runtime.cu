@@ -36,6 +36,7 @@
 #include "gf_layout.h"
 #include "gf_internal.h"
 #include "gf_program.h"
+#include "host/range_alloc.h"
 #include "host/server.h"
 
 #define GF_MAX_BLOCKS_PER_SM 32
@@ -72,52 +73,6 @@ extern "C" __attribute__((visibility("default"))) int gf_program_register(const 
 }
 
 /* ------------------------------------------------------------------ context */
-/* First-fit allocator of unit ranges in [0, total): the heap pool in 256 KiB
- * slabs, the ring pool in slots.  Callers hold the context's admission lock. */
-struct RangeAlloc {
-    uint64_t total = 0;
-    std::map<uint64_t, uint64_t> free_;   /* start -> length, disjoint, not touching */
-    void init(uint64_t n)
-    {
-        total = n;
-        free_.clear();
-        if (n)
-            free_[0] = n;
-    }
-    bool alloc(uint64_t n, uint64_t *out)
-    {
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second < n)
-                continue;
-            const uint64_t a = it->first, l = it->second;
-            free_.erase(it);
-            if (l > n)
-                free_[a + n] = l - n;
-            *out = a;
-            return true;
-        }
-        return false;
-    }
-    void release(uint64_t a, uint64_t n)
-    {
-        if (!n)
-            return;
-        auto it = free_.emplace(a, n).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && a + n == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-};
-
 struct Staged {
     void *host;
     void *dev;
