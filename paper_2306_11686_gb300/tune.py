@@ -5,8 +5,11 @@ Pipeline (the learned-model pattern on top of the runtime):
      natively (gf_synth_time: CUDA events, fastest of `reps` runs after a
      warm-up); its per-loop optimum is the reference regret is measured
      against.
-  2. `train`: an FP32 MLP (3 hidden layers of 64 ReLU units) learns log(ms)
-     from gf_tune_features(loop, shape) on the training loops (torch).
+  2. `train`: an FP32 MLP (3 hidden layers of 64 ReLU units) learns, from
+     gf_tune_features(loop, shape) on the training loops (torch), the log of
+     a shape's time relative to that loop's fastest shape: only the ranking
+     of a loop's shapes matters for the choice, and removing each loop's own
+     scale leaves the network the shape effects to fit.
   3. `evaluate`: on held-out loops the model's choice (gf_mlp_choose, the C++
      forward pass) is compared with the autotuner's optimum:
      regret = t(model's shape) / t(best measured shape) - 1; also against the
@@ -259,7 +262,7 @@ def evaluate(params, loops, shs, ms, sms, refine_k=3, ctx=None, x=None, z=None, 
              autotuner's choice -- the fair comparison.  Needs ctx, x, z."""
     h = shs.index(heuristic_shape(sms))
     res = {"n": len(loops), "refine_k": refine_k}
-    t1, tr, th = [], [], []
+    t1, tr, th, trand = [], [], [], []
     retimed = {"top1": [], "refined": [], "plain": []}
     for k, d in enumerate(loops):
         cand = topk(params, d, shs, sms, refine_k)
@@ -270,6 +273,7 @@ def evaluate(params, loops, shs, ms, sms, refine_k=3, ctx=None, x=None, z=None, 
         t1.append(float(ms[k, c1]) / best - 1.0)
         tr.append(float(ms[k, cr]) / best - 1.0)
         th.append(float(ms[k, h]) / best - 1.0)
+        trand.append(float(np.mean(ms[k])) / best - 1.0)     # a shape drawn uniformly at random
         if ctx is not None:
             picks = [c1, cr, auto, h]
             sa = c_shapes([shs[s] for s in picks])
@@ -282,7 +286,7 @@ def evaluate(params, loops, shs, ms, sms, refine_k=3, ctx=None, x=None, z=None, 
             retimed["top1"].append(row[0] / ta - 1.0)
             retimed["refined"].append(row[1] / ta - 1.0)
             retimed["plain"].append(row[3] / ta - 1.0)
-    res["table"] = {"top1": _stats(t1), "refined": _stats(tr), "plain": _stats(th)}
+    res["table"] = {"top1": _stats(t1), "refined": _stats(tr), "plain": _stats(th), "random": _stats(trand)}
     if ctx is not None:
         res["retimed"] = {k: _stats(v) for k, v in retimed.items()}
         res["learned_vs_plain_speedup_geomean"] = float(np.exp(np.mean(
@@ -304,7 +308,8 @@ def run(n_loops=2000, n_train=1600, reps=2, epochs=300, out=None, log=print):
     ms = measure(ctx, loops, shs, x, z, reps=reps, log=log)
     t_meas = time.time() - t0
     X = np.concatenate([features(d, shs, sms) for d in loops[:n_train]])
-    y = np.log(np.maximum(ms[:n_train].reshape(-1), 1e-4))
+    lm = np.log(np.maximum(ms[:n_train], 1e-4))
+    y = (lm - lm.min(axis=1, keepdims=True)).reshape(-1)     # log time relative to the loop's fastest shape
     params = train(X, y, epochs=epochs, log=log)
     res = evaluate(params, loops[n_train:], shs, ms[n_train:], sms, ctx=ctx, x=x, z=z)
     res.update({"loops": n_loops, "train": n_train, "shapes": len(shs), "reps": reps,
