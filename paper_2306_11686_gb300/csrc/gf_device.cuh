@@ -63,6 +63,22 @@ __shared__ uint32_t s_kr;                  /* 1 outside a program's persistent k
 __shared__ uint64_t s_red[GF_MAX_WARPS][2];/* per-warp reduction partials               */
 __shared__ uint64_t s_xfer[GF_MAX_WARPS][32]; /* per-warp lane hand-off (heap, rpc)    */
 
+/* A ring slot that lane groups of one warp arriving at the same call
+ * separately (divergent groups) can share: its opener keeps it open for a
+ * short window, other groups with the same call signature append their
+ * records, and one publication serves them all (gf_device_rpc.cuh). */
+struct join_slot {
+    unsigned long long ctl;   /* state (bits 62-63) | generation (40-61) | records (32-39) | bytes (0-31) */
+    unsigned long long sig;   /* call signature of the open slot                                   */
+    unsigned long long slot;  /* device address of the ring slot                                   */
+    unsigned long long ticket;
+    uint32_t fbytes;          /* inline format bytes at the payload's start                        */
+    int32_t writers;          /* lanes that reserved a record and have not yet written it          */
+    int32_t readers;          /* lanes that have not yet read their return                          */
+    int32_t done;             /* 0 while pending, 1 answered, < 0 the error                         */
+};
+__shared__ join_slot s_join[GF_MAX_WARPS];
+
 /* how long the initial thread polls a region's end without sleeping, and
  * the workers poll for the next region with short sleeps */
 #define GF_REGION_SPIN_NS 20000u
@@ -119,6 +135,22 @@ __device__ __forceinline__ uint32_t smid()
 }
 
 __device__ __forceinline__ gf_state *st() { return s_st; }
+
+/* Thread 0 of every block of a kernel that uses the device runtime: the
+ * program's state, whether this is a program's persistent kernel (kr = 0)
+ * or another kernel whose threads are all workers (kr = 1), and the block's
+ * shared slots all free.  Followed by __syncthreads() in the caller. */
+__device__ __forceinline__ void block_setup(gf_state *S, uint32_t kr)
+{
+    s_st = S;
+    s_kr = kr;
+    for (int w = 0; w < GF_MAX_WARPS; w++) {
+        s_join[w].ctl = 0ull;
+        s_join[w].writers = 0;
+        s_join[w].readers = 0;
+        s_join[w].done = 0;
+    }
+}
 __device__ __forceinline__ bool is_initial_thread() { return blockIdx.x == 0 && threadIdx.x == 0 && !s_kr; }
 
 __device__ __forceinline__ void set_error(int e)
@@ -778,10 +810,8 @@ typedef int (*main_t)(int, char **);
 template <main_t MAIN, int MINB = GF_MIN_BLOCKS>
 __global__ void __launch_bounds__(GF_BLOCK, MINB) program_kernel(gf_state *S, int argc, char **argv)
 {
-    if (threadIdx.x == 0) {
-        s_st = S;
-        s_kr = 0;
-    }
+    if (threadIdx.x == 0)
+        block_setup(S, 0);
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x < 32) {
         if (threadIdx.x == 0) {
@@ -812,8 +842,7 @@ template <main_t MAIN, int MINB = GF_MIN_BLOCKS>
 __global__ void __launch_bounds__(GF_BLOCK, MINB) region_kernel(gf_state *S)
 {
     if (threadIdx.x == 0) {
-        s_st = S;
-        s_kr = 1;
+        block_setup(S, 1);
         s_abort = *(volatile int32_t *)&S->error != 0;   /* one reading for the whole block */
     }
     __syncthreads();

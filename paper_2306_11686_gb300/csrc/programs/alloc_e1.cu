@@ -22,8 +22,7 @@ __global__ void __launch_bounds__(256) e1_kernel(gf_state *S, gfpa::balanced B, 
 {
     if (KIND == 0) {
         if (threadIdx.x == 0) {
-            gfd::s_st = S;
-            gfd::s_kr = 1;      /* not a program kernel: every thread is a worker */
+            gfd::block_setup(S, 1);    /* not a program kernel: every thread is a worker */
         }
         __syncthreads();
     }

@@ -139,8 +139,7 @@ __global__ void __launch_bounds__(GF_BLOCK) loop_rpc_kernel(loop_rpc_body B, dou
                                                              int k, gf_state *S)
 {
     if (threadIdx.x == 0) {
-        gfd::s_st = S;
-        gfd::s_kr = 1;          /* not a program kernel: every thread is a worker */
+        gfd::block_setup(S, 1);    /* not a program kernel: every thread is a worker */
     }
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

@@ -40,8 +40,7 @@ __global__ void __launch_bounds__(1024) synth_kernel(SynthP P, const double *__r
                                                      gf_state *S, unsigned long long *counter)
 {
     if (threadIdx.x == 0) {
-        gfd::s_st = S;
-        gfd::s_kr = 1;          /* not a program kernel: every thread is a worker */
+        gfd::block_setup(S, 1);    /* not a program kernel: every thread is a worker */
     }
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31u;

@@ -746,21 +746,18 @@ extern "C" GF_API int gf_launch_q(gf_ctx *c, gf_program prog, int argc, const ch
     for (int k = 0; k < nbufs; k++) {
         cudaPointerAttributes at;
         void *dev = bufs[k].ptr;
-        bool owned = false;
         if (bufs[k].ptr && bufs[k].bytes) {
             if (cudaPointerGetAttributes(&at, bufs[k].ptr) != cudaSuccess)
                 return bail(GF_EINVAL);
             if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) {
                 if (cudaMallocAsync(&dev, bufs[k].bytes, h->stream) != cudaSuccess)
                     return bail(GF_ENOMEM);
-                owned = true;
                 h->staged.push_back({bufs[k].ptr, dev, bufs[k].bytes, bufs[k].dir, true});
                 if ((bufs[k].dir & GF_BUF_IN) &&
                     cudaMemcpyAsync(dev, bufs[k].ptr, bufs[k].bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
                     return bail(GF_ECUDA);
             }
         }
-        (void)owned;
         s.buf_ptr[k] = (uint64_t)dev;
         s.buf_bytes[k] = bufs[k].bytes;
     }
