@@ -76,6 +76,7 @@ struct join_slot {
     int32_t writers;          /* lanes that reserved a record and have not yet written it          */
     int32_t readers;          /* lanes that have not yet read their return                          */
     int32_t done;             /* 0 while pending, 1 answered, < 0 the error                         */
+    uint32_t hint;            /* 1: the warp's last shared slot was joined, so hold the next open  */
 };
 __shared__ join_slot s_join[GF_MAX_WARPS];
 
@@ -149,6 +150,7 @@ __device__ __forceinline__ void block_setup(gf_state *S, uint32_t kr)
         s_join[w].writers = 0;
         s_join[w].readers = 0;
         s_join[w].done = 0;
+        s_join[w].hint = 1;
     }
 }
 __device__ __forceinline__ bool is_initial_thread() { return blockIdx.x == 0 && threadIdx.x == 0 && !s_kr; }
