@@ -274,9 +274,10 @@ __device__ __forceinline__ unsigned long long js_make(unsigned long long st, uns
  * slot's control word and writes its records there.  The opener then closes
  * the slot, waits until every reserved record is written, publishes once,
  * waits for the host, hands each group its returns and gives the slot back
- * when every lane has read its own.  No warp-wide synchronisation is
- * involved: the groups meet only through shared-memory atomics, and every
- * wait is bounded.  Returns 1 when the call was served this way (*ret and
+ * when every lane has read its own.  A warp whose last shared slot drew no
+ * other group skips the window, so lone callers do not wait for it.  No
+ * warp-wide synchronisation is involved: the groups meet only through
+ * shared-memory atomics, and every wait is bounded.  Returns 1 when the call was served this way (*ret and
  * *st set), 0 when the caller takes the ordinary path.
  */
 static __device__ __noinline__ int rpc_join(uint32_t op, const char *fmt, const argpack &a, uint64_t sig, uint32_t grp,
@@ -433,8 +434,12 @@ static __device__ __noinline__ int rpc_join(uint32_t op, const char *fmt, const 
     int wst = GF_OK;
     uint32_t nl = n_g;
     if (lane == leader) {
-        /* the window: other groups of this warp may still join */
-        while (js_count(VJ->ctl) < 32u && now_ns() - t_open < GF_JOIN_WINDOW_NS)
+        /* the window: other groups of this warp may still join.  A warp
+         * whose last shared slot found no joiner (lone callers, such as one
+         * printing lane per loop chunk) publishes at once instead, until a
+         * group joins again during the short time its slot is open */
+        const uint64_t win = VJ->hint ? GF_JOIN_WINDOW_NS : 0u;
+        while (js_count(VJ->ctl) < 32u && now_ns() - t_open < win)
             __nanosleep(64);
         unsigned long long v = VJ->ctl;
         for (;;) {
@@ -444,6 +449,7 @@ static __device__ __noinline__ int rpc_join(uint32_t op, const char *fmt, const 
             v = c;
         }
         nl = js_count(v);
+        VJ->hint = nl > n_g ? 1u : 0u;
         backoff bo(S->timeout_ns);
         while (VJ->writers != 0)                  /* every reserved record written */
             if (!bo.wait()) {
