@@ -54,6 +54,15 @@ def test_strerror_and_defaults_without_gpu(lib):
         gf.gf_config_default(ctypes.byref(bad))
         bad.split_regions, bad.server_threads = split, threads
         assert gf.gf_init(ctypes.byref(bad), ctypes.byref(h)) == gf.GF_EINVAL
+    # admission pools: 0 = the default quota times max_programs; a pool that
+    # cannot hold one default quota is refused before any device work
+    assert c.heap_pool_bytes == 0 and c.ring_pool_slots == 0
+    for field, value in (("heap_pool_bytes", 1 << 20), ("ring_pool_slots", 2048)):
+        bad = gf.gf_config()
+        gf.gf_config_default(ctypes.byref(bad))
+        setattr(bad, field, value)                          # below heap_bytes (4 GiB) / ring_slots (4096)
+        assert gf.gf_init(ctypes.byref(bad), ctypes.byref(h)) == gf.GF_EINVAL
+    assert ctypes.sizeof(gf.gf_quota) == 16
 
 
 def test_programs_registered(lib):
