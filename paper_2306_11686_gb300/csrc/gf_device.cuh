@@ -76,9 +76,12 @@ struct join_slot {
     int32_t writers;          /* lanes that reserved a record and have not yet written it          */
     int32_t readers;          /* lanes that have not yet read their return                          */
     int32_t done;             /* 0 while pending, 1 answered, < 0 the error                         */
-    uint32_t hint;            /* 1: the warp's last shared slot was joined, so hold the next open  */
 };
-__shared__ join_slot s_join[GF_MAX_WARPS];
+/* a warp's shared slots: one may be open for joining while others wait
+ * for the host's answer */
+#define GF_JOIN_SLOTS 4
+__shared__ join_slot s_join[GF_MAX_WARPS][GF_JOIN_SLOTS];
+__shared__ uint32_t s_join_hint[GF_MAX_WARPS];  /* 1: the warp's last shared slot was joined */
 
 /* how long the initial thread polls a region's end without sleeping, and
  * the workers poll for the next region with short sleeps */
@@ -146,11 +149,13 @@ __device__ __forceinline__ void block_setup(gf_state *S, uint32_t kr)
     s_st = S;
     s_kr = kr;
     for (int w = 0; w < GF_MAX_WARPS; w++) {
-        s_join[w].ctl = 0ull;
-        s_join[w].writers = 0;
-        s_join[w].readers = 0;
-        s_join[w].done = 0;
-        s_join[w].hint = 1;
+        for (int d = 0; d < GF_JOIN_SLOTS; d++) {
+            s_join[w][d].ctl = 0ull;
+            s_join[w][d].writers = 0;
+            s_join[w][d].readers = 0;
+            s_join[w][d].done = 0;
+        }
+        s_join_hint[w] = 1;
     }
 }
 __device__ __forceinline__ bool is_initial_thread() { return blockIdx.x == 0 && threadIdx.x == 0 && !s_kr; }

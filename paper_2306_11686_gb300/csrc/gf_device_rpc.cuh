@@ -284,9 +284,7 @@ static __device__ __noinline__ int rpc_join(uint32_t op, const char *fmt, const 
                                             uint32_t gtid, int64_t *ret_out, int *st_out)
 {
     gf_state *S = s_st;
-    const uint32_t lane = lane_id();
-    join_slot &J = s_join[threadIdx.x >> 5];
-    volatile join_slot *VJ = &J;
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     const uint32_t leader = __ffs(grp) - 1, n_g = __popc(grp), rank = __popc(grp & lanemask_lt());
     const uint32_t my = a.bytes();
     const uint64_t key = (uint64_t)fmt;
@@ -300,35 +298,49 @@ static __device__ __noinline__ int rpc_join(uint32_t op, const char *fmt, const 
     }
     const uint32_t slot_cap = S->slot_bytes - GF_SLOT_PAYLOAD_OFF;
     int mode = 0;                                 /* 1 joined, 2 opened */
-    uint32_t base_idx = 0, base_off = 0;
+    uint32_t jd = 0, base_idx = 0, base_off = 0;
     unsigned long long gen = 0;
     if (lane == leader) {
-        atomicAdd(&J.writers, (int)n_g);          /* before the reservation: a closing opener waits for it */
-        __threadfence_block();
-        const unsigned long long v = VJ->ctl;
-        if (js_state(v) == GF_JS_OPEN) {
+        /* join an open slot of this warp with the same call signature */
+        for (uint32_t d = 0; d < GF_JOIN_SLOTS && !mode; d++) {
+            join_slot &C = s_join[warp][d];
+            volatile join_slot *VC = &C;
+            const unsigned long long v = VC->ctl;
+            if (js_state(v) != GF_JS_OPEN)
+                continue;
             __threadfence_block();
-            if (VJ->sig == sig && js_count(v) + n_g <= 32u && VJ->fbytes + js_bytes(v) + tot <= slot_cap &&
-                atomicCAS(&J.ctl, v, v + ((unsigned long long)n_g << 32) + tot) == v) {
+            if (VC->sig != sig || js_count(v) + n_g > 32u || VC->fbytes + js_bytes(v) + tot > slot_cap)
+                continue;
+            atomicAdd(&C.writers, (int)n_g);      /* before the reservation: a closing opener waits for it */
+            __threadfence_block();
+            if (atomicCAS(&C.ctl, v, v + ((unsigned long long)n_g << 32) + tot) == v) {
                 mode = 1;
+                jd = d;
                 base_idx = js_count(v);
                 base_off = js_bytes(v);
+            } else {
+                atomicSub(&C.writers, (int)n_g);
             }
         }
-        if (mode == 0) {
-            const unsigned long long v2 = VJ->ctl;
-            if (js_state(v2) == GF_JS_FREE && tot <= slot_cap &&
-                atomicCAS(&J.ctl, v2, js_make(GF_JS_OPENING, js_gen(v2), 0, 0)) == v2) {
-                mode = 2;                         /* the group's own n_g writers stay counted */
+        /* or open a free one */
+        for (uint32_t d = 0; d < GF_JOIN_SLOTS && !mode && tot <= slot_cap; d++) {
+            join_slot &C = s_join[warp][d];
+            const unsigned long long v2 = *(volatile unsigned long long *)&C.ctl;
+            if (js_state(v2) == GF_JS_FREE &&
+                atomicCAS(&C.ctl, v2, js_make(GF_JS_OPENING, js_gen(v2), 0, 0)) == v2) {
+                atomicAdd(&C.writers, (int)n_g);  /* the group's own records */
+                mode = 2;
+                jd = d;
                 gen = js_gen(v2) + 1;
-            } else {
-                atomicSub(&J.writers, (int)n_g);
             }
         }
     }
     mode = __shfl_sync(grp, mode, leader);
     if (mode == 0)
         return 0;
+    jd = __shfl_sync(grp, jd, leader);
+    join_slot &J = s_join[warp][jd];
+    volatile join_slot *VJ = &J;
     int64_t ret = -1;
     int st = GF_OK;
     if (mode == 1) {
@@ -438,7 +450,7 @@ static __device__ __noinline__ int rpc_join(uint32_t op, const char *fmt, const 
          * whose last shared slot found no joiner (lone callers, such as one
          * printing lane per loop chunk) publishes at once instead, until a
          * group joins again during the short time its slot is open */
-        const uint64_t win = VJ->hint ? GF_JOIN_WINDOW_NS : 0u;
+        const uint64_t win = *(volatile uint32_t *)&s_join_hint[warp] ? GF_JOIN_WINDOW_NS : 0u;
         while (js_count(VJ->ctl) < 32u && now_ns() - t_open < win)
             __nanosleep(64);
         unsigned long long v = VJ->ctl;
@@ -449,7 +461,7 @@ static __device__ __noinline__ int rpc_join(uint32_t op, const char *fmt, const 
             v = c;
         }
         nl = js_count(v);
-        VJ->hint = nl > n_g ? 1u : 0u;
+        *(volatile uint32_t *)&s_join_hint[warp] = nl > n_g ? 1u : 0u;
         backoff bo(S->timeout_ns);
         while (VJ->writers != 0)                  /* every reserved record written */
             if (!bo.wait()) {

@@ -83,6 +83,29 @@ GF_MAIN(rpc_storm)(int argc, char **argv)
     return rc ? 10 : 0;
 }
 
+/* rpc_diverge n                      buffers: 0 = int32 returns[n]
+ * Odd and even iterations print from two different call sites with one
+ * format, so the lanes of a warp reach the call as two separate groups (the
+ * shared-slot path lets the second join the first's slot). */
+__device__ const char rpc_diverge_fmt[] = "d %lld %d\n";
+GF_MAIN(rpc_diverge)(int argc, char **argv)
+{
+    if (argc < 2)
+        return 2;
+    const long long n = gf_atoll(argv[1]);
+    int *ret = (int *)gf_buffer(0);
+    if (!ret || gf_buffer_bytes(0) < (uint64_t)n * 4)
+        return 2;
+    return gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) {
+        int r;
+        if (i & 1)
+            r = gf_printf(rpc_diverge_fmt, (long long)i, 1);
+        else
+            r = gf_printf(rpc_diverge_fmt, (long long)i, 0);
+        ret[i] = r;
+    }) ? 10 : 0;
+}
+
 /* link_probe bytes reps dir         buffers: 0 = device bytes, 1 = int64 ns[reps]
  * Times `reps` grid-wide copies of `bytes` between device memory and the
  * context's bulk arena (pinned host memory mapped into the device): dir 0 =

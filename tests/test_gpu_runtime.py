@@ -175,6 +175,32 @@ def test_rpc_storm_order_and_multiset(gf_lib, tmp_path, aggregate):
         assert st.rpc_slots[gf.OP_PRINTF] == st.rpc_calls[gf.OP_PRINTF]
 
 
+@pytest.mark.parametrize("aggregate", [1, 0])
+def test_rpc_divergent_groups_share_slots(gf_lib, tmp_path, aggregate):
+    """Odd and even lanes print from two call sites with one format: every
+    line and return value as printf gives them, and with aggregation a slot
+    holds at least a half warp's records (the two call sites' groups either
+    share a slot or the compiler merged the sites)."""
+    import torch
+    gf = gf_lib
+    n = 20000 + 13
+    ret = torch.zeros(n, dtype=torch.int32, device="cuda")
+    with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20,
+                    aggregate=aggregate, server_threads=2) as c:
+        rc, ec = c.run("rpc_diverge", [n], [(ret, 1)])
+        st = c.stats()
+    assert ec == 0
+    want = ["d %d %d" % (i, i & 1) for i in range(n)]
+    assert sorted(open(tmp_path / "out.txt").read().splitlines()) == sorted(want)
+    assert ret.cpu().tolist() == [len(w) + 1 for w in want]
+    calls, slots = int(st.rpc_calls[gf.OP_PRINTF]), int(st.rpc_slots[gf.OP_PRINTF])
+    assert calls == n
+    if aggregate:
+        assert calls >= 16 * slots, (calls, slots)
+    else:
+        assert slots == calls
+
+
 def test_heap_audit(gf_lib, tmp_path):
     import torch
     gf = gf_lib
