@@ -63,26 +63,6 @@ __shared__ uint32_t s_kr;                  /* 1 outside a program's persistent k
 __shared__ uint64_t s_red[GF_MAX_WARPS][2];/* per-warp reduction partials               */
 __shared__ uint64_t s_xfer[GF_MAX_WARPS][32]; /* per-warp lane hand-off (heap, rpc)    */
 
-/* A ring slot that lane groups of one warp arriving at the same call
- * separately (divergent groups) can share: its opener keeps it open for a
- * short window, other groups with the same call signature append their
- * records, and one publication serves them all (gf_device_rpc.cuh). */
-struct join_slot {
-    unsigned long long ctl;   /* state (bits 62-63) | generation (40-61) | records (32-39) | bytes (0-31) */
-    unsigned long long sig;   /* call signature of the open slot                                   */
-    unsigned long long slot;  /* device address of the ring slot                                   */
-    unsigned long long ticket;
-    uint32_t fbytes;          /* inline format bytes at the payload's start                        */
-    int32_t writers;          /* lanes that reserved a record and have not yet written it          */
-    int32_t readers;          /* lanes that have not yet read their return                          */
-    int32_t done;             /* 0 while pending, 1 answered, < 0 the error                         */
-};
-/* a warp's shared slots: one may be open for joining while others wait
- * for the host's answer */
-#define GF_JOIN_SLOTS 4
-__shared__ join_slot s_join[GF_MAX_WARPS][GF_JOIN_SLOTS];
-__shared__ uint32_t s_join_hint[GF_MAX_WARPS];  /* 1: the warp's last shared slot was joined */
-
 /* how long the initial thread polls a region's end without sleeping, and
  * the workers poll for the next region with short sleeps */
 #define GF_REGION_SPIN_NS 20000u
@@ -141,22 +121,13 @@ __device__ __forceinline__ uint32_t smid()
 __device__ __forceinline__ gf_state *st() { return s_st; }
 
 /* Thread 0 of every block of a kernel that uses the device runtime: the
- * program's state, whether this is a program's persistent kernel (kr = 0)
- * or another kernel whose threads are all workers (kr = 1), and the block's
- * shared slots all free.  Followed by __syncthreads() in the caller. */
+ * program's state, and whether this is a program's persistent kernel
+ * (kr = 0) or another kernel whose threads are all workers (kr = 1).
+ * Followed by __syncthreads() in the caller. */
 __device__ __forceinline__ void block_setup(gf_state *S, uint32_t kr)
 {
     s_st = S;
     s_kr = kr;
-    for (int w = 0; w < GF_MAX_WARPS; w++) {
-        for (int d = 0; d < GF_JOIN_SLOTS; d++) {
-            s_join[w][d].ctl = 0ull;
-            s_join[w][d].writers = 0;
-            s_join[w][d].readers = 0;
-            s_join[w][d].done = 0;
-        }
-        s_join_hint[w] = 1;
-    }
 }
 __device__ __forceinline__ bool is_initial_thread() { return blockIdx.x == 0 && threadIdx.x == 0 && !s_kr; }
 

@@ -245,311 +245,6 @@ static __device__ __noinline__ int rpc_collect_deferred(gf_state *S)
     return GF_OK;
 }
 
-/* ---------------------------------------------------------------- shared slots of a warp */
-/* How long the lane group that opened a shared slot waits for the warp's
- * other groups to join it before publishing. */
-#define GF_JOIN_WINDOW_NS 2000u
-#define GF_JS_FREE 0ull
-#define GF_JS_OPENING 1ull
-#define GF_JS_OPEN 2ull
-#define GF_JS_CLOSED 3ull
-__device__ __forceinline__ unsigned long long js_state(unsigned long long v) { return v >> 62; }
-__device__ __forceinline__ unsigned long long js_gen(unsigned long long v) { return (v >> 40) & 0x3fffffull; }
-__device__ __forceinline__ uint32_t js_count(unsigned long long v) { return (uint32_t)(v >> 32) & 0xffu; }
-__device__ __forceinline__ uint32_t js_bytes(unsigned long long v) { return (uint32_t)v; }
-__device__ __forceinline__ unsigned long long js_make(unsigned long long st, unsigned long long gen, uint32_t cnt,
-                                                      uint32_t bytes)
-{
-    return (st << 62) | ((gen & 0x3fffffull) << 40) | ((unsigned long long)cnt << 32) | bytes;
-}
-
-/*
- * Warp aggregation across divergent groups.  Lanes of one warp that reach
- * the same call at different times (after divergent code such as the
- * heap's per-class paths) arrive as separate groups and would each take a
- * slot.  Here the first group opens a shared slot of its warp (s_join):
- * it claims a ring ticket, writes its records and keeps the slot open for
- * GF_JOIN_WINDOW_NS or until 32 records are in; a later group with the same
- * call signature reserves room in it with one compare-and-swap on the
- * slot's control word and writes its records there.  The opener then closes
- * the slot, waits until every reserved record is written, publishes once,
- * waits for the host, hands each group its returns and gives the slot back
- * when every lane has read its own.  A warp whose last shared slot drew no
- * other group skips the window, so lone callers do not wait for it.  No
- * warp-wide synchronisation is involved: the groups meet only through
- * shared-memory atomics, and every wait is bounded.  Returns 1 when the call was served this way (*ret and
- * *st set), 0 when the caller takes the ordinary path.
- */
-static __device__ __noinline__ int rpc_join(uint32_t op, const char *fmt, const argpack &a, uint64_t sig, uint32_t grp,
-                                            uint32_t gtid, int64_t *ret_out, int *st_out)
-{
-    gf_state *S = s_st;
-    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    const uint32_t leader = __ffs(grp) - 1, n_g = __popc(grp), rank = __popc(grp & lanemask_lt());
-    const uint32_t my = a.bytes();
-    const uint64_t key = (uint64_t)fmt;
-    uint32_t off = 0, tot = 0;                    /* exclusive prefix of record bytes, group total */
-    for (uint32_t m = grp; m; m &= m - 1) {
-        const uint32_t l = __ffs(m) - 1;
-        const uint32_t x = __shfl_sync(grp, my, l);
-        if (l < lane)
-            off += x;
-        tot += x;
-    }
-    const uint32_t slot_cap = S->slot_bytes - GF_SLOT_PAYLOAD_OFF;
-    int mode = 0;                                 /* 1 joined, 2 opened */
-    uint32_t jd = 0, base_idx = 0, base_off = 0;
-    unsigned long long gen = 0;
-    if (lane == leader) {
-        /* join an open slot of this warp with the same call signature */
-        for (uint32_t d = 0; d < GF_JOIN_SLOTS && !mode; d++) {
-            join_slot &C = s_join[warp][d];
-            volatile join_slot *VC = &C;
-            const unsigned long long v = VC->ctl;
-            if (js_state(v) != GF_JS_OPEN)
-                continue;
-            __threadfence_block();
-            if (VC->sig != sig || js_count(v) + n_g > 32u || VC->fbytes + js_bytes(v) + tot > slot_cap)
-                continue;
-            atomicAdd(&C.writers, (int)n_g);      /* before the reservation: a closing opener waits for it */
-            __threadfence_block();
-            if (atomicCAS(&C.ctl, v, v + ((unsigned long long)n_g << 32) + tot) == v) {
-                mode = 1;
-                jd = d;
-                base_idx = js_count(v);
-                base_off = js_bytes(v);
-            } else {
-                atomicSub(&C.writers, (int)n_g);
-            }
-        }
-        /* or open a free one */
-        for (uint32_t d = 0; d < GF_JOIN_SLOTS && !mode && tot <= slot_cap; d++) {
-            join_slot &C = s_join[warp][d];
-            const unsigned long long v2 = *(volatile unsigned long long *)&C.ctl;
-            if (js_state(v2) == GF_JS_FREE &&
-                atomicCAS(&C.ctl, v2, js_make(GF_JS_OPENING, js_gen(v2), 0, 0)) == v2) {
-                atomicAdd(&C.writers, (int)n_g);  /* the group's own records */
-                mode = 2;
-                jd = d;
-                gen = js_gen(v2) + 1;
-            }
-        }
-    }
-    mode = __shfl_sync(grp, mode, leader);
-    if (mode == 0)
-        return 0;
-    jd = __shfl_sync(grp, jd, leader);
-    join_slot &J = s_join[warp][jd];
-    volatile join_slot *VJ = &J;
-    int64_t ret = -1;
-    int st = GF_OK;
-    if (mode == 1) {
-        /* ---- joined: write the records into the open slot, wait for the opener's answer */
-        unsigned long long slot = 0;
-        uint32_t fb = 0;
-        if (lane == leader) {
-            __threadfence_block();
-            slot = VJ->slot;
-            fb = VJ->fbytes;
-        }
-        slot = __shfl_sync(grp, slot, leader);
-        fb = __shfl_sync(grp, fb, leader);
-        base_idx = __shfl_sync(grp, base_idx, leader);
-        base_off = __shfl_sync(grp, base_off, leader);
-        uint8_t *payload = (uint8_t *)slot + GF_SLOT_PAYLOAD_OFF;
-        write_rec(payload + fb + base_off + off, a, lane, gtid);
-        __threadfence_system();                   /* this record is visible to the host before it counts as written */
-        atomicSub(&J.writers, 1);
-        int d = 0;
-        if (lane == leader) {
-            backoff bo(S->timeout_ns);
-            while ((d = VJ->done) == 0)
-                if (!bo.wait()) {
-                    d = GF_ETIMEDOUT;
-                    set_error(GF_ETIMEDOUT);
-                    break;
-                }
-            __threadfence_block();
-        }
-        d = __shfl_sync(grp, d, leader);
-        if (d == 1) {
-            ret = (int64_t)ld_vol64((const uint64_t *)((uint8_t *)slot + GF_SLOT_RET_OFF) + base_idx + rank);
-            const uint64_t *rw = (const uint64_t *)(payload + fb + base_off + off);
-            const uint32_t ntag = (a.n + 7u) & ~7u;
-            const uint64_t *tail = rw + 2 + ntag / 8 + a.n;
-            for (uint32_t k = 0; k < a.n; k++)
-                if (a.tag[k] == GF_T_BLOB_W || a.tag[k] == GF_T_BLOB_RW)
-                    copy_back((void *)a.src[k], tail + (uint32_t)(a.word[k] & 0xffffu) / 8, a.len[k]);
-        } else {
-            st = d;
-        }
-        atomicSub(&J.readers, 1);
-        *ret_out = ret;
-        *st_out = st;
-        return 1;
-    }
-    /* ---- opened: claim a ring slot, let other groups join, publish once */
-    unsigned long long t = 0, slot = 0;
-    uint32_t fb = 0, fmt_len = 0;
-    int ship = 0, cst = GF_OK;
-    uint64_t t_issue = 0, t_open = 0;
-    if (lane == leader) {
-        ship = (fmt && !fmt_known(S, key)) ? 1 : 0;
-        fmt_len = ship ? gf_strlen(fmt) + 1u : 0u;
-        fb = ship ? ((fmt_len + 7u) & ~7u) : 0u;
-        if (fb + tot > slot_cap) {
-            cst = GF_EINVAL;                      /* no room beside the format: the ordinary path splits it */
-        } else {
-            t_issue = now_ns();
-            t = atomicAdd(&S->rpc_ticket, 1ull);
-            slot = S->ring_slots + (t % S->nslots) * (uint64_t)S->slot_bytes;
-            backoff bo(S->timeout_ns);
-            while (ld_acq_sys64((const uint64_t *)slot) != t)
-                if (!bo.wait()) {
-                    cst = GF_ERING;
-                    set_error(GF_ERING);
-                    break;
-                }
-        }
-        if (cst != GF_OK) {
-            atomicSub(&J.writers, (int)n_g);
-            __threadfence_block();
-            VJ->ctl = js_make(GF_JS_FREE, gen, 0, 0);
-        } else {
-            VJ->sig = sig;
-            VJ->slot = slot;
-            VJ->ticket = t;
-            VJ->fbytes = fb;
-            VJ->readers = 0;
-            VJ->done = 0;
-            __threadfence_block();
-            t_open = now_ns();
-            VJ->ctl = js_make(GF_JS_OPEN, gen, n_g, tot);   /* from here other groups may join */
-        }
-    }
-    cst = __shfl_sync(grp, cst, leader);
-    if (cst == GF_EINVAL)
-        return 0;
-    if (cst != GF_OK) {
-        *ret_out = -1;
-        *st_out = cst;
-        return 1;
-    }
-    slot = __shfl_sync(grp, slot, leader);
-    fb = __shfl_sync(grp, fb, leader);
-    uint8_t *payload = (uint8_t *)slot + GF_SLOT_PAYLOAD_OFF;
-    gf_slot_hdr *h = (gf_slot_hdr *)slot;
-    write_rec(payload + fb + off, a, lane, gtid);
-    __threadfence_system();
-    atomicSub(&J.writers, 1);
-    __syncwarp(grp);
-    int wst = GF_OK;
-    uint32_t nl = n_g;
-    if (lane == leader) {
-        /* the window: other groups of this warp may still join.  A warp
-         * whose last shared slot found no joiner (lone callers, such as one
-         * printing lane per loop chunk) publishes at once instead, until a
-         * group joins again during the short time its slot is open */
-        const uint64_t win = *(volatile uint32_t *)&s_join_hint[warp] ? GF_JOIN_WINDOW_NS : 0u;
-        while (js_count(VJ->ctl) < 32u && now_ns() - t_open < win)
-            __nanosleep(64);
-        unsigned long long v = VJ->ctl;
-        for (;;) {
-            const unsigned long long c = atomicCAS(&J.ctl, v, (v & ~(3ull << 62)) | (GF_JS_CLOSED << 62));
-            if (c == v)
-                break;
-            v = c;
-        }
-        nl = js_count(v);
-        *(volatile uint32_t *)&s_join_hint[warp] = nl > n_g ? 1u : 0u;
-        backoff bo(S->timeout_ns);
-        while (VJ->writers != 0)                  /* every reserved record written */
-            if (!bo.wait()) {
-                wst = GF_ETIMEDOUT;
-                set_error(GF_ETIMEDOUT);
-                break;
-            }
-        if (wst == GF_OK) {
-            __threadfence_system();
-            if (ship)
-                copy_out((uint64_t *)payload, fmt, fmt_len);
-            h->opcode = op;
-            h->nlanes = nl;
-            h->flags = ship ? GF_SF_FMT_INLINE : 0u;
-            h->fmt_len = ship ? fmt_len : 0u;
-            h->fmt_key = key;
-            h->prog = S->prog_id;
-            h->t_issue = t_issue;
-            h->payload_bytes = 0;
-            h->t_publish = now_ns();
-            st_rel_sys64(&h->seq, t + 1);
-            backoff bw(S->timeout_ns);
-            const uint64_t t0 = now_ns();
-            while (ld_acq_sys64(&h->seq) != t + 2)
-                if (!bw.wait()) {
-                    wst = GF_ETIMEDOUT;
-                    set_error(GF_ETIMEDOUT);
-                    break;
-                }
-            const uint64_t waited = now_ns() - t0;
-            atomicAdd((unsigned long long *)&S->st_wait_ns, (unsigned long long)waited);
-            atomicAdd((unsigned long long *)&S->st_wait_op_ns[op < GF_NSTAT ? op : 0], (unsigned long long)waited);
-            if (wst == GF_OK) {
-                const uint64_t lat = now_ns() - t_issue;
-                uint32_t bk = (uint32_t)lat;
-                if (lat >= 8) {
-                    const uint32_t e = 63 - __clzll((long long)lat);
-                    bk = 8u * e + (uint32_t)((lat >> (e - 3)) & 7u);
-                }
-                if (bk >= GF_LAT_BUCKETS)
-                    bk = GF_LAT_BUCKETS - 1;
-                atomicAdd((unsigned long long *)&S->lat_hist[bk], (unsigned long long)nl);
-                atomicAdd((unsigned long long *)&S->st_calls[op < GF_NSTAT ? op : 0], (unsigned long long)nl);
-                atomicAdd((unsigned long long *)&S->st_slots[op < GF_NSTAT ? op : 0], 1ull);
-            }
-        }
-        VJ->readers = (int)nl;
-        __threadfence_block();
-        VJ->done = wst == GF_OK ? 1 : wst;
-    }
-    wst = __shfl_sync(grp, wst, leader);
-    if (wst == GF_OK) {
-        ret = (int64_t)ld_vol64((const uint64_t *)((uint8_t *)slot + GF_SLOT_RET_OFF) + rank);
-        const uint64_t *rw = (const uint64_t *)(payload + fb + off);
-        const uint32_t ntag = (a.n + 7u) & ~7u;
-        const uint64_t *tail = rw + 2 + ntag / 8 + a.n;
-        for (uint32_t k = 0; k < a.n; k++)
-            if (a.tag[k] == GF_T_BLOB_W || a.tag[k] == GF_T_BLOB_RW)
-                copy_back((void *)a.src[k], tail + (uint32_t)(a.word[k] & 0xffffu) / 8, a.len[k]);
-    } else {
-        st = wst;
-    }
-    atomicSub(&J.readers, 1);
-    __syncwarp(grp);
-    if (lane == leader) {
-        if (wst == GF_OK) {
-            backoff br(S->timeout_ns);
-            bool all_read = true;
-            while (VJ->readers > 0)               /* every lane has read its return */
-                if (!br.wait()) {
-                    all_read = false;
-                    set_error(GF_ETIMEDOUT);
-                    break;
-                }
-            if (all_read) {
-                if (ship)
-                    fmt_insert(S, key);
-                st_rel_sys64(&h->seq, t + S->nslots);
-            }
-        }
-        __threadfence_block();
-        VJ->ctl = js_make(GF_JS_FREE, gen, 0, 0);
-    }
-    *ret_out = ret;
-    *st_out = st;
-    return 1;
-}
-
 /*
  * Issue one RPC from every calling lane; returns this lane's host result.
  * *status receives GF_OK, GF_ERING (no slot credit within the timeout),
@@ -587,17 +282,6 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
     const uint32_t my = a.bytes();
     const uint32_t gtid = is_initial_thread() ? 0xffffffffu : (uint32_t)gf_thread_num();
     const uint32_t slot_cap = S->slot_bytes - GF_SLOT_PAYLOAD_OFF;
-    /* a group smaller than the warp shares a slot with the warp's other
-     * groups making the same call (region threads, aggregation on) */
-    if (S->aggregate && !initial && !defer_t1 && grp != 0xffffffffu && (threadIdx.x >> 5) < GF_MAX_WARPS) {
-        int64_t jr = -1;
-        int jst = GF_OK;
-        if (rpc_join(op, fmt, a, sig, grp, gtid, &jr, &jst)) {
-            if (status)
-                *status = jst;
-            return jr;
-        }
-    }
 
     uint32_t remaining = grp;
     int64_t ret = -1;
