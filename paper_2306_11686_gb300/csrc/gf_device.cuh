@@ -62,6 +62,14 @@ __shared__ uint32_t s_kr;                  /* 1 outside a program's persistent k
                                               the initial thread, ids have no offset   */
 __shared__ uint64_t s_red[GF_MAX_WARPS][2];/* per-warp reduction partials               */
 __shared__ uint64_t s_xfer[GF_MAX_WARPS][32]; /* per-warp lane hand-off (heap, rpc)    */
+/* the initial thread's own bookkeeping, kept in its block's shared memory so
+ * that its serial part pays no global-memory round trip for it: */
+__shared__ uint32_t s_done_target;         /* blocks done when the current region ends   */
+__shared__ unsigned long long s_pend_t1;   /* deferred call: ticket + 1, 0 = none        */
+__shared__ unsigned long long s_pend_key;  /* ... and the format it shipped (0: none)    */
+__shared__ unsigned long long s_done_t1;   /* last deferred call collected with its value */
+__shared__ long long s_done_val;
+__shared__ unsigned long long s_known_key; /* a format the host is known to have         */
 
 /* how long the initial thread polls a region's end without sleeping, and
  * the workers poll for the next region with short sleeps */
@@ -128,6 +136,12 @@ __device__ __forceinline__ void block_setup(gf_state *S, uint32_t kr)
 {
     s_st = S;
     s_kr = kr;
+    s_done_target = 0;
+    s_pend_t1 = 0;
+    s_pend_key = 0;
+    s_done_t1 = 0;
+    s_done_val = -1;
+    s_known_key = 0;
 }
 __device__ __forceinline__ bool is_initial_thread() { return blockIdx.x == 0 && threadIdx.x == 0 && !s_kr; }
 
@@ -452,7 +466,7 @@ static __device__ __noinline__ int run_region(gf_state *S)
 {
     if (*(volatile int32_t *)&S->error)      /* after a timeout the workers may still be busy */
         return S->error;
-    S->st_regions++;
+    atomicAdd((unsigned long long *)&S->st_regions, 1ull);   /* no result needed: no round trip */
     if (S->split) {
         /* the paper's kernel split (Sec. 3.3, Fig. 3): one RPC per region, on
          * which the host launches the region as its own kernel; the initial
@@ -467,8 +481,8 @@ static __device__ __noinline__ int run_region(gf_state *S)
             set_error(st != GF_OK ? st : GF_ECUDA);
             return S->error;
         }
-        const uint32_t target = S->done_target + (uint32_t)grid;
-        S->done_target = target;
+        const uint32_t target = s_done_target + (uint32_t)grid;
+        s_done_target = target;
         backoff bo(S->timeout_ns);
         while ((int32_t)(ld_acq_gpu(&S->done_blocks) - target) < 0) {
             if (now_ns() - t0 < GF_REGION_SPIN_NS)
@@ -478,11 +492,11 @@ static __device__ __noinline__ int run_region(gf_state *S)
                 return GF_ETIMEDOUT;
             }
         }
-        S->st_region_ns += now_ns() - t0;
+        atomicAdd((unsigned long long *)&S->st_region_ns, (unsigned long long)(now_ns() - t0));
         return GF_OK;
     }
-    const uint32_t target = S->done_target + S->nblocks;
-    S->done_target = target;
+    const uint32_t target = s_done_target + S->nblocks;
+    s_done_target = target;
     S->dyn_next = 0;
     S->red_ticket = 0;
     const uint64_t t0 = now_ns();
@@ -497,7 +511,7 @@ static __device__ __noinline__ int run_region(gf_state *S)
             return GF_ETIMEDOUT;
         }
     }
-    S->st_region_ns += now_ns() - t0;
+    atomicAdd((unsigned long long *)&S->st_region_ns, (unsigned long long)(now_ns() - t0));
     return GF_OK;
 }
 
@@ -795,7 +809,7 @@ __global__ void __launch_bounds__(GF_BLOCK, MINB) program_kernel(gf_state *S, in
         if (threadIdx.x == 0) {
             S->t_main_start = now_ns();
             int rc = MAIN(argc, argv);
-            rpc_collect_deferred(S);     /* a printf main did not wait for */
+            rpc_collect_deferred(S, false);   /* a printf main did not wait for */
             S->exit_code = rc;
             S->t_main_end = now_ns();
             S->main_done = 1;

@@ -433,7 +433,7 @@ static __device__ __noinline__ void *gf_malloc(size_t n)
     const uint64_t t0 = timed ? gfd::now_ns() : 0;
     void *p = gf_malloc_body(n);
     if (timed)
-        gfd::s_st->st_heap_ns += gfd::now_ns() - t0;
+        atomicAdd((unsigned long long *)&gfd::s_st->st_heap_ns, (unsigned long long)(gfd::now_ns() - t0));
     return p;
 }
 
@@ -443,7 +443,7 @@ static __device__ __noinline__ void gf_free(void *p)
     const uint64_t t0 = timed ? gfd::now_ns() : 0;
     gf_free_body(p);
     if (timed)
-        gfd::s_st->st_heap_ns += gfd::now_ns() - t0;
+        atomicAdd((unsigned long long *)&gfd::s_st->st_heap_ns, (unsigned long long)(gfd::now_ns() - t0));
 }
 
 /* size of the heap block holding p (0 if p is not a live heap block start) */

@@ -208,18 +208,27 @@ __device__ inline void fmt_insert(gf_state *S, uint64_t key)
     }
 }
 
-/*
- * The initial thread's outstanding deferred call: wait (bounded) until the
- * host has answered it, keep its result in the state, give its slot back.
- * Initial thread only.
- */
-static __device__ __noinline__ int rpc_collect_deferred(gf_state *S)
+__device__ __forceinline__ void st_relaxed_sys64(uint64_t *p, uint64_t v)
 {
-    const unsigned long long t1 = S->pend_ticket1;
+    asm volatile("st.relaxed.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+/*
+ * The initial thread's outstanding deferred call (a printf-family call):
+ * wait (bounded) until the host has answered it, give its slot back, and
+ * return the nanoseconds waited.  With want_ret its result is kept for a
+ * gf_call_result converted now (a round trip more, and the slot is given
+ * back with a release so the read stays before it); from the thread's next
+ * RPC the result is not read, and the give-back needs no ordering beyond
+ * the acquire that saw the answer.  Initial thread only.
+ */
+static __device__ __noinline__ uint64_t rpc_collect_deferred(gf_state *S, bool want_ret)
+{
+    const unsigned long long t1 = s_pend_t1;
     if (!t1)
-        return GF_OK;
+        return 0;
     const unsigned long long t = t1 - 1;
-    S->pend_ticket1 = 0;
+    s_pend_t1 = 0;
     uint8_t *slot = (uint8_t *)(S->ring_slots + (t % S->nslots) * (uint64_t)S->slot_bytes);
     gf_slot_hdr *h = (gf_slot_hdr *)slot;
     const uint64_t t0 = now_ns();
@@ -227,22 +236,29 @@ static __device__ __noinline__ int rpc_collect_deferred(gf_state *S)
     while (ld_acq_sys64(&h->seq) != t + 2)
         if (!bo.wait()) {
             set_error(GF_ETIMEDOUT);
-            S->done_ticket1 = t1;
-            S->done_val = -1;
-            return GF_ETIMEDOUT;
+            s_done_t1 = t1;
+            s_done_val = -1;
+            return now_ns() - t0;
         }
-    S->done_val = (int64_t)ld_vol64((const uint64_t *)(slot + GF_SLOT_RET_OFF));
-    S->done_ticket1 = t1;
-    const uint32_t op = h->opcode;
     const uint64_t waited = now_ns() - t0;
-    S->st_wait_ns += waited;
-    S->st_wait_op_ns[op < GF_NSTAT ? op : 0] += waited;
-    S->st_calls[op < GF_NSTAT ? op : 0]++;
-    S->st_slots[op < GF_NSTAT ? op : 0]++;
-    if (S->pend_fmt_key)
-        fmt_insert(S, S->pend_fmt_key);
-    st_rel_sys64(&h->seq, t + S->nslots);
-    return GF_OK;
+    const uint32_t op = GF_OP_PRINTF;            /* the only deferred calls */
+    atomicAdd((unsigned long long *)&S->st_wait_ns, (unsigned long long)waited);
+    atomicAdd((unsigned long long *)&S->st_wait_op_ns[op], (unsigned long long)waited);
+    atomicAdd((unsigned long long *)&S->st_calls[op], 1ull);
+    atomicAdd((unsigned long long *)&S->st_slots[op], 1ull);
+    if (s_pend_key) {
+        fmt_insert(S, s_pend_key);
+        s_known_key = s_pend_key;
+    }
+    if (want_ret) {
+        s_done_val = (long long)ld_vol64((const uint64_t *)(slot + GF_SLOT_RET_OFF));
+        s_done_t1 = t1;
+        st_rel_sys64(&h->seq, t + S->nslots);
+    } else {
+        s_done_t1 = 0;
+        st_relaxed_sys64(&h->seq, t + S->nslots);
+    }
+    return waited;
 }
 
 /*
@@ -262,11 +278,8 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
     const bool initial = is_initial_thread();
     const uint64_t t_enter = initial ? now_ns() : 0;
     uint64_t t_waited = 0;                          /* this call's waits for the host */
-    if (initial && S->pend_ticket1) {               /* keep the initial thread's calls in order */
-        const uint64_t w0 = S->st_wait_ns;
-        rpc_collect_deferred(S);
-        t_waited += S->st_wait_ns - w0;
-    }
+    if (initial && s_pend_t1)                       /* keep the initial thread's calls in order */
+        t_waited += rpc_collect_deferred(S, false);
     {
         /* fail fast after the first error; one reading for the whole group */
         const int err = __shfl_sync(active, *(volatile int32_t *)&S->error, __ffs(active) - 1);
@@ -293,7 +306,10 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
         int ship = 0;
         uint32_t fmt_len = 0;
         if (lane == rl) {
-            ship = (fmt && !fmt_known(S, key)) ? 1 : 0;
+            /* the initial thread remembers the last format it knows the host has */
+            ship = (fmt && !(initial && key == s_known_key) && !fmt_known(S, key)) ? 1 : 0;
+            if (initial && fmt && !ship)
+                s_known_key = key;
             fmt_len = ship ? gf_strlen(fmt) + 1u : 0u;      /* read the format only to ship it */
         }
         ship = __shfl_sync(grp, ship, rl);
@@ -385,8 +401,8 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
             h->payload_bytes = 0;
             h->t_publish = now_ns();
             st_rel_sys64(&h->seq, t + 1);
-            S->pend_ticket1 = t + 1;
-            S->pend_fmt_key = ship ? key : 0;
+            s_pend_t1 = t + 1;
+            s_pend_key = ship ? key : 0;
             *defer_t1 = t + 1;
             ret = 0;
             continue;
@@ -438,13 +454,16 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
         }
         __syncwarp(grp);
         if (lane == leader && wst == GF_OK) {
-            if (ship)
+            if (ship) {
                 fmt_insert(S, key);
+                if (initial)
+                    s_known_key = key;
+            }
             st_rel_sys64(&h->seq, t + S->nslots);
         }
     }
     if (initial)
-        S->st_client_ns += now_ns() - t_enter - t_waited;
+        atomicAdd((unsigned long long *)&S->st_client_ns, (unsigned long long)(now_ns() - t_enter - t_waited));
     if (status)
         *status = st;
     return ret;
@@ -461,16 +480,16 @@ template <class... A> __device__ inline int64_t rpc(uint32_t op, const char *fmt
 static __device__ __noinline__ int64_t deferred_value(unsigned long long t1)
 {
     gf_state *S = s_st;
-    if (S->pend_ticket1 == t1)
-        rpc_collect_deferred(S);
-    return S->done_ticket1 == t1 ? S->done_val : -1;
+    if (s_pend_t1 == t1)
+        rpc_collect_deferred(S, true);
+    return s_done_t1 == t1 ? (int64_t)s_done_val : -1;
 }
 } // namespace gfd
 
 /* Result of a printf-family call.  Converting it to int gives the call's
  * return value (waiting for the host if the call was deferred); a program
  * that ignores it never waits for the call.  Use it in the statement that
- * made the call: a deferred result read after two or more later RPCs of the
+ * made the call: a deferred result converted after a later RPC of the
  * initial thread reads -1. */
 struct gf_call_result {
     int64_t v;
@@ -505,8 +524,8 @@ static __device__ __noinline__ int rpc_post1(uint32_t op, const argpack &a, unsi
     gf_state *S = s_st;
     if (a.bytes() > S->slot_bytes - GF_SLOT_PAYLOAD_OFF)
         return GF_EINVAL;
-    if (S->pend_ticket1)
-        rpc_collect_deferred(S);
+    if (s_pend_t1)
+        rpc_collect_deferred(S, false);
     if (*(volatile int32_t *)&S->error)
         return S->error;
     const unsigned long long t = atomicAdd(&S->rpc_ticket, 1ull);

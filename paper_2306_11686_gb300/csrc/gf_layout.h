@@ -195,11 +195,6 @@ typedef struct gf_state {
     uint32_t split;            /* 1: regions run as host-launched kernels (the paper's split) */
     /* results written by the device */
     int32_t exit_code, error, main_done;
-    /* the initial thread's deferred call (printf family, result not yet
-     * needed): ticket + 1, 0 = none; the last one collected and its result */
-    uint64_t pend_ticket1, pend_fmt_key;
-    uint64_t done_ticket1;
-    int64_t done_val;
     uint64_t st_calls[GF_NSTAT];  /* RPC calls per opcode (lane records)              */
     uint64_t st_slots[GF_NSTAT];  /* ring slots per opcode                            */
     uint64_t st_wait_ns;          /* device ns spent waiting for the host             */

@@ -60,10 +60,9 @@ GF_MAIN(axpy_sum)(int argc, char **argv)
  * with an invariant-divisor magic number.
  */
 template <int INT_ADDS>
-__device__ int jacobi_sweep(const double *u, double *un, uint32_t nn, uint64_t cells, double *res)
+__device__ int jacobi_sweep(const double *u, double *un, uint32_t nn, gf_udiv32 dn, uint64_t cells, double *res)
 {
     const uint32_t sk = nn * nn;
-    const gf_udiv32 dn = gf_udiv32::make(nn);
     return gf_reduce<double, GF_RED_MAX>(
         0, (int64_t)cells, GF_SCHED_STATIC, 1,
         [=](int64_t c64) -> double {
@@ -102,11 +101,11 @@ __device__ int jacobi_sweep(const double *u, double *un, uint32_t nn, uint64_t c
  * and the residual are the same bits.
  */
 template <int INT_ADDS>
-__device__ int jacobi_sweep_col(const double *u, double *un, uint32_t nn, uint32_t kseg, double *res)
+__device__ int jacobi_sweep_col(const double *u, double *un, uint32_t nn, gf_udiv32 dn, gf_udiv32 dsk, uint32_t kseg,
+                                double *res)
 {
     const uint32_t sk = nn * nn;
     const uint32_t nseg = (nn + kseg - 1) / kseg;
-    const gf_udiv32 dn = gf_udiv32::make(nn), dsk = gf_udiv32::make(sk);
     return gf_reduce<double, GF_RED_MAX>(
         0, (int64_t)nseg * sk, GF_SCHED_STATIC, 1,
         [=](int64_t t64) -> double {
@@ -184,6 +183,8 @@ GF_MAIN_BOUNDS(jacobi, 4)(int argc, char **argv)
     const uint32_t nn = (uint32_t)n;
     const double *u = u0;
     double *owned = nullptr;
+    /* the index split's magic numbers: loop invariants, made once */
+    const gf_udiv32 dn = gf_udiv32::make(nn), dsk = gf_udiv32::make(nn * nn);
     for (int s = 1; s <= sweeps; s++) {
         double *un = (double *)gf_malloc(cells * sizeof(double));
         if (!un) {
@@ -195,21 +196,21 @@ GF_MAIN_BOUNDS(jacobi, 4)(int argc, char **argv)
         if (kseg > 0) {
             const uint32_t ks = (uint32_t)kseg;
             switch (int_adds) {
-            case 0: rc = jacobi_sweep_col<0>(u, un, nn, ks, &res); break;
-            case 1: rc = jacobi_sweep_col<1>(u, un, nn, ks, &res); break;
-            case 2: rc = jacobi_sweep_col<2>(u, un, nn, ks, &res); break;
-            case 3: rc = jacobi_sweep_col<3>(u, un, nn, ks, &res); break;
-            case 4: rc = jacobi_sweep_col<4>(u, un, nn, ks, &res); break;
-            default: rc = jacobi_sweep_col<5>(u, un, nn, ks, &res); break;
+            case 0: rc = jacobi_sweep_col<0>(u, un, nn, dn, dsk, ks, &res); break;
+            case 1: rc = jacobi_sweep_col<1>(u, un, nn, dn, dsk, ks, &res); break;
+            case 2: rc = jacobi_sweep_col<2>(u, un, nn, dn, dsk, ks, &res); break;
+            case 3: rc = jacobi_sweep_col<3>(u, un, nn, dn, dsk, ks, &res); break;
+            case 4: rc = jacobi_sweep_col<4>(u, un, nn, dn, dsk, ks, &res); break;
+            default: rc = jacobi_sweep_col<5>(u, un, nn, dn, dsk, ks, &res); break;
             }
         } else {
             switch (int_adds) {
-            case 0: rc = jacobi_sweep<0>(u, un, nn, cells, &res); break;
-            case 1: rc = jacobi_sweep<1>(u, un, nn, cells, &res); break;
-            case 2: rc = jacobi_sweep<2>(u, un, nn, cells, &res); break;
-            case 3: rc = jacobi_sweep<3>(u, un, nn, cells, &res); break;
-            case 4: rc = jacobi_sweep<4>(u, un, nn, cells, &res); break;
-            default: rc = jacobi_sweep<5>(u, un, nn, cells, &res); break;
+            case 0: rc = jacobi_sweep<0>(u, un, nn, dn, cells, &res); break;
+            case 1: rc = jacobi_sweep<1>(u, un, nn, dn, cells, &res); break;
+            case 2: rc = jacobi_sweep<2>(u, un, nn, dn, cells, &res); break;
+            case 3: rc = jacobi_sweep<3>(u, un, nn, dn, cells, &res); break;
+            case 4: rc = jacobi_sweep<4>(u, un, nn, dn, cells, &res); break;
+            default: rc = jacobi_sweep<5>(u, un, nn, dn, cells, &res); break;
             }
         }
         if (rc)
