@@ -225,19 +225,27 @@ static __device__ uint32_t heap_bump(gf_heap *H, uint32_t sm, uint32_t cls, uint
 }
 
 /* ---------------------------------------------------------------- large path */
+/* the large path's lock: an acquiring compare-and-swap takes it and a
+ * releasing store gives it back, which order the extent table's reads and
+ * writes inside it without full fences */
+__device__ __forceinline__ uint32_t cas_acquire_gpu(uint32_t *p, uint32_t cmp, uint32_t val)
+{
+    uint32_t old;
+    asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;"
+                 : "=r"(old) : "l"(p), "r"(cmp), "r"(val) : "memory");
+    return old;
+}
 static __device__ bool large_lock(gf_heap *H, int64_t timeout_ns)
 {
     backoff bo(timeout_ns);
-    while (atomicCAS(&H->large_lock, 0u, 1u) != 0u)
+    while (cas_acquire_gpu(&H->large_lock, 0u, 1u) != 0u)
         if (!bo.wait())
             return false;
-    __threadfence();
     return true;
 }
 static __device__ void large_unlock(gf_heap *H)
 {
-    __threadfence();
-    atomicExch(&H->large_lock, 0u);
+    st_rel_gpu(&H->large_lock, 0u);
 }
 
 static __device__ void *large_alloc(gf_heap *H, uint64_t n, int64_t timeout_ns)
