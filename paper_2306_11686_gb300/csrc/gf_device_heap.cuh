@@ -294,23 +294,30 @@ static __device__ bool large_free(gf_heap *H, uint64_t addr, int64_t timeout_ns)
     }
     sz[pg] = 0;
     uint32_t cnt = *(volatile uint32_t *)&H->large_next;
+    /* the free extents around pg, each read from the table once: the lock
+     * holder is the only writer, so the copies stay current */
     uint32_t k = 0;
-    while (k < cnt && (uint32_t)ext[k] < pg)
-        k++;
+    uint64_t prev = 0, cur = 0;
+    for (; k < cnt; k++) {
+        cur = ext[k];
+        if ((uint32_t)cur >= pg)
+            break;
+        prev = cur;
+    }
     uint32_t start = pg, len = np;
-    const bool merge_prev = k > 0 && (uint32_t)ext[k - 1] + (uint32_t)(ext[k - 1] >> 32) == pg;
-    const bool merge_next = k < cnt && pg + np == (uint32_t)ext[k];
+    const bool merge_prev = k > 0 && (uint32_t)prev + (uint32_t)(prev >> 32) == pg;
+    const bool merge_next = k < cnt && pg + np == (uint32_t)cur;
     if (merge_prev && merge_next) {
-        start = (uint32_t)ext[k - 1];
-        len = (uint32_t)(ext[k - 1] >> 32) + np + (uint32_t)(ext[k] >> 32);
+        start = (uint32_t)prev;
+        len = (uint32_t)(prev >> 32) + np + (uint32_t)(cur >> 32);
         ext[k - 1] = (uint64_t)start | ((uint64_t)len << 32);
         for (uint32_t q = k; q + 1 < cnt; q++)
             ext[q] = ext[q + 1];
         cnt--;
     } else if (merge_prev) {
-        ext[k - 1] = (uint64_t)(uint32_t)ext[k - 1] | ((uint64_t)((uint32_t)(ext[k - 1] >> 32) + np) << 32);
+        ext[k - 1] = (uint64_t)(uint32_t)prev | ((uint64_t)((uint32_t)(prev >> 32) + np) << 32);
     } else if (merge_next) {
-        ext[k] = (uint64_t)pg | ((uint64_t)(np + (uint32_t)(ext[k] >> 32)) << 32);
+        ext[k] = (uint64_t)pg | ((uint64_t)(np + (uint32_t)(cur >> 32)) << 32);
     } else if (cnt < GF_LARGE_EXT_MAX) {
         for (uint32_t q = cnt; q > k; q--)
             ext[q] = ext[q - 1];
