@@ -178,7 +178,8 @@ typedef struct gf_state {
     unsigned long long rpc_ticket; uint64_t pad_t[15]; /* ring ticket counter            */
     gf_region region;
     uint64_t red_result[2];
-    uint32_t done_target, exit_flag;
+    uint32_t exit_flag;        /* main returned: the workers leave their loop            */
+    uint32_t pad_x;
     /* configuration written by the host before launch */
     uint32_t nblocks, block_dim, nworkers, aggregate;
     int64_t timeout_ns;
