@@ -36,9 +36,9 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the division by 6, the residual's subtract.
 FP64_OPS_PER_POINT = 7
 # DRAM bytes (read + write) of one full launch, scaled from an ncu capture of
-# the current program kernel (20 sweeps, no final write: 3.1818 + 3.0993 GB,
-# 314.05 MB per sweep) to 100 sweeps plus the final fwrite's 134.2 MB read.
-TRAFFIC_PER_LAUNCH = 100 * 314_054_050 + 134_217_728
+# the current program kernel (20 sweeps, no final write: 3.1817 + 3.0988 GB,
+# 314.03 MB per sweep) to 100 sweeps plus the final fwrite's 134.2 MB read.
+TRAFFIC_PER_LAUNCH = 100 * 314_025_370 + 134_217_728
 
 
 def fp64_pipe_ops_per_point(int_adds):
