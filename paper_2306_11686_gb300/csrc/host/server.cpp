@@ -242,44 +242,42 @@ FILE *Server::file_of(uint64_t h)
     return files_.count(h) ? (FILE *)(uintptr_t)h : nullptr;
 }
 
-void Server::emit(uint64_t stream, const std::string &s)
+void Server::emit(uint64_t stream, const char *s, size_t n)
 {
-    if (s.empty())
+    if (!n)
         return;
     FILE *f = file_of(stream);
     if (!f)
         return;
     std::lock_guard<std::mutex> g(out_mu_);
-    fwrite(s.data(), 1, s.size(), f);
+    fwrite(s, 1, n, f);
 }
 
 /*
- * printf landing pad: walk the format, and for each conversion call snprintf
- * with exactly that conversion and an argument of the C type it names.  The
- * output equals one printf call with the same arguments, because printf's
- * output is the concatenation of its literal text and its conversions.
- * Plain conversions (no flags, width or '*') go through gfh::fmt_fast
- * (std::to_chars, the same characters) instead of snprintf.
+ * printf landing pad.  The format is cut once into literal runs and
+ * conversions (compile_fmt); each record then appends the literals and, for
+ * each conversion, snprintf with exactly that conversion and an argument of
+ * the C type it names.  The output equals one printf call with the same
+ * arguments, because printf's output is the concatenation of its literal
+ * text and its conversions.  Plain conversions (no flags, width or '*') go
+ * through gfh::fmt_fast (std::to_chars, the same characters) instead of
+ * snprintf.
  */
-int64_t Server::do_printf(const char *fmt, const uint8_t *recp, std::string &out, uint64_t *stream)
+FmtPlan compile_fmt(const char *fmt)
 {
-    RecView r(recp);
-    if (r.nargs < 1 || !fmt)
-        return -1;
-    *stream = r.word(0);
-    uint32_t ai = 1;
-    const size_t start = out.size();
-    char spec[64], buf[512];
+    FmtPlan pl;
+    FmtConv c;
+    c.lit_off = 0;
     for (const char *p = fmt; *p;) {
         if (*p != '%') {
             const char *q = strchr(p, '%');
-            size_t n = q ? (size_t)(q - p) : strlen(p);
-            out.append(p, n);
+            const size_t n = q ? (size_t)(q - p) : strlen(p);
+            pl.lits.append(p, n);
             p += n;
             continue;
         }
         if (p[1] == '%') {
-            out.push_back('%');
+            pl.lits.push_back('%');
             p += 2;
             continue;
         }
@@ -289,9 +287,8 @@ int64_t Server::do_printf(const char *fmt, const uint8_t *recp, std::string &out
             p++;
         const bool flags = p != s0 + 1;
         bool width = false;
-        int star_w = 0, star_p = 0, prec = -1;
         if (*p == '*') {
-            star_w = 1;
+            c.star_w = true;
             p++;
         } else
             while (*p >= '0' && *p <= '9') {
@@ -301,33 +298,62 @@ int64_t Server::do_printf(const char *fmt, const uint8_t *recp, std::string &out
         if (*p == '.') {
             p++;
             if (*p == '*') {
-                star_p = 1;
+                c.star_p = true;
                 p++;
             } else {
-                prec = 0;
+                c.prec = 0;
                 while (*p >= '0' && *p <= '9') {
-                    prec = prec < 100000 ? prec * 10 + (*p - '0') : prec;
+                    c.prec = c.prec < 100000 ? c.prec * 10 + (*p - '0') : c.prec;
                     p++;
                 }
             }
         }
-        char len[3] = {0, 0, 0};
         if (*p == 'h' || *p == 'l') {
-            len[0] = *p++;
-            if (*p == len[0])
-                len[1] = *p++;
+            c.len[0] = *p++;
+            if (*p == c.len[0])
+                c.len[1] = *p++;
         } else if (*p == 'j' || *p == 'z' || *p == 't' || *p == 'L' || *p == 'q') {
-            len[0] = *p++;
+            c.len[0] = *p++;
         }
-        const char conv = *p;
-        if (!conv)
+        if (!*p)                        /* a conversion cut off by the end: output stops here */
             break;
-        p++;
-        size_t sl = (size_t)(p - s0);
-        if (sl >= sizeof(spec))
+        c.conv = *p++;
+        c.lit_len = (uint32_t)pl.lits.size() - c.lit_off;
+        c.spec.assign(s0, (size_t)(p - s0));
+        c.bad = c.spec.size() >= 64;
+        c.plain = !flags && !width && !c.star_w && !c.star_p;
+        pl.convs.push_back(c);
+        if (c.bad)
+            return pl;
+        c = FmtConv();
+        c.lit_off = (uint32_t)pl.lits.size();
+    }
+    c.conv = 0;
+    c.lit_len = (uint32_t)pl.lits.size() - c.lit_off;
+    pl.convs.push_back(c);
+    return pl;
+}
+
+int64_t Server::do_printf(const FmtPlan &pl, const uint8_t *recp, OutBuf &out, uint64_t *stream)
+{
+    RecView r(recp);
+    if (r.nargs < 1)
+        return -1;
+    *stream = r.word(0);
+    uint32_t ai = 1;
+    const size_t start = out.size();
+    char buf[512];
+    const size_t FAST = 512;             /* room for any conversion fmt_fast takes */
+    for (const FmtConv &c : pl.convs) {
+        out.append(pl.lits.data() + c.lit_off, c.lit_len);
+        if (!c.conv)
+            break;
+        if (c.bad)
             return -1;
-        memcpy(spec, s0, sl);
-        spec[sl] = 0;
+        const char *spec = c.spec.c_str();
+        const char conv = c.conv;
+        const char *len = c.len;
+        const bool star_w = c.star_w, star_p = c.star_p;
         int wv = 0, pv = 0;
         if (star_w) {
             if (ai >= r.nargs)
@@ -349,9 +375,8 @@ int64_t Server::do_printf(const char *fmt, const uint8_t *recp, std::string &out
         const uint32_t k = ai++;
         const uint64_t w = r.word(k);
         int n = 0;
-        if (!flags && !width && !star_w && !star_p &&
-            gfh::fmt_fast(conv, len, prec, w, r.tag(k) == GF_T_F64, buf, sizeof(buf), &n)) {
-            out.append(buf, (size_t)n);
+        if (c.plain && gfh::fmt_fast(conv, len, c.prec, w, r.tag(k) == GF_T_F64, out.room(FAST), FAST, &n)) {
+            out.commit((size_t)n);
             continue;
         }
         char *dst = buf;
@@ -434,7 +459,7 @@ int64_t Server::do_printf(const char *fmt, const uint8_t *recp, std::string &out
             GF_FMT((void *)(uintptr_t)w);
             break;
         default:
-            out.append(spec);
+            out.append(spec, c.spec.size());
             continue;
         }
 #undef GF_FMT
@@ -449,13 +474,15 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
     RecView r(rec);
     switch (op) {
     case GF_OP_PRINTF: {
-        std::string s;
+        if (!fmt)
+            return -1;
+        OutBuf s;
         uint64_t stream = 0;
-        int64_t n = do_printf(fmt, rec, s, &stream);
+        int64_t n = do_printf(compile_fmt(fmt), rec, s, &stream);
         if (n >= 0) {
             if (!file_of(stream))
                 return -1;
-            emit(stream, s);
+            emit(stream, s.data(), s.size());
         }
         return n;
     }
@@ -585,6 +612,14 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
     }
 }
 
+/* each server thread's text buffer, kept between passes so it is not
+ * reallocated for every pass */
+static OutBuf &tl_out()
+{
+    thread_local OutBuf b;
+    return b;
+}
+
 int Server::poll(Segment &seg, uint32_t tid, uint32_t nthr)
 {
     /* announce this poller before looking at `active`: whoever clears
@@ -607,20 +642,21 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
     /* printf text of consecutive slots to one stream is written in one go;
      * those slots are released only after their text reached the stream, so
      * one device thread's calls still appear in program order */
-    std::string out;
+    OutBuf &out = tl_out();
+    out.clear();
     uint64_t out_stream = 0;
     uint64_t *held[16];
     uint64_t held_t[16];
     uint32_t nheld = 0;
     auto flush = [&]() {
         if (!out.empty())
-            emit(out_stream, out);
+            emit(out_stream, out.data(), out.size());
         out.clear();
         for (uint32_t k = 0; k < nheld; k++)
             release_store(held[k], held_t[k]);
         nheld = 0;
     };
-    std::unordered_map<uint64_t, const std::string *> *local =
+    std::unordered_map<uint64_t, const FmtEntry *> *local =
         tid < seg.fmt_local.size() ? &seg.fmt_local[tid] : nullptr;
     /* Claims arrive in ticket order, so the next request is usually in the
      * slot after the last one served: start there and stop after a run of
@@ -643,36 +679,37 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
         const uint64_t t0 = now_ns();
         const uint32_t op = h->opcode, nl = h->nlanes;
         uint8_t *pay = slot + GF_SLOT_PAYLOAD_OFF;
-        const char *fmt = nullptr;
+        const FmtEntry *fe = nullptr;
         if (h->flags & GF_SF_FMT_INLINE) {
             const char *inl = (const char *)pay;
-            const std::string *str;
             {
                 std::lock_guard<std::mutex> g(seg.fmt_mu);
-                str = &seg.fmt_cache.emplace(h->fmt_key, std::string(inl, strnlen(inl, h->fmt_len))).first->second;
+                auto ins = seg.fmt_cache.try_emplace(h->fmt_key);
+                if (ins.second) {          /* first sight: keep the text and its compiled form */
+                    ins.first->second.text.assign(inl, strnlen(inl, h->fmt_len));
+                    ins.first->second.plan = compile_fmt(ins.first->second.text.c_str());
+                }
+                fe = &ins.first->second;
             }
             if (local)
-                (*local)[h->fmt_key] = str;
-            fmt = str->c_str();
+                (*local)[h->fmt_key] = fe;
             pay += (h->fmt_len + 7u) & ~7u;
         } else if (h->fmt_key) {
-            const std::string *str = nullptr;
             if (local) {
                 auto it = local->find(h->fmt_key);
                 if (it != local->end())
-                    str = it->second;
+                    fe = it->second;
             }
-            if (!str) {
+            if (!fe) {
                 std::lock_guard<std::mutex> g(seg.fmt_mu);
                 auto it = seg.fmt_cache.find(h->fmt_key);
                 if (it != seg.fmt_cache.end()) {
-                    str = &it->second;
+                    fe = &it->second;
                     if (local)
-                        (*local)[h->fmt_key] = str;
+                        (*local)[h->fmt_key] = fe;
                 }
             }
             /* a key never shipped: printf answers -1 per lane (no format) */
-            fmt = str ? str->c_str() : nullptr;
         }
         int64_t *ret = (int64_t *)(slot + GF_SLOT_RET_OFF);
         const uint8_t *end = slot + seg.slot_bytes;
@@ -701,19 +738,19 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
                     stream = st;
                     first = false;
                 }
-                ret[l] = fmt ? do_printf(fmt, pay, out, &st) : -1;
+                ret[l] = fe ? do_printf(fe->plan, pay, out, &st) : -1;
                 if (st != stream) {                    /* lanes writing to different streams */
-                    const std::string tail = out.substr(before);
-                    out.resize(before);
+                    const std::string tail(out.data() + before, out.size() - before);
+                    out.shrink(before);
                     flush();
-                    out = tail;
+                    out.append(tail.data(), tail.size());
                     out_stream = stream = st;
                 }
                 pay += rh->bytes;
             }
             if (!first && !file_of(stream)) {
                 bad_stream = true;
-                out.resize(std::min(out.size(), mark));
+                out.shrink(mark);
             }
             if (bad_stream)
                 for (uint32_t l = 0; l < nl && l < 32; l++)
@@ -727,7 +764,7 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
                     ret[l] = -1;
                     continue;
                 }
-                ret[l] = call(op, fmt, pay, &seg);
+                ret[l] = call(op, fe ? fe->text.c_str() : nullptr, pay, &seg);
                 pay += rh->bytes;
             }
         }

@@ -20,6 +20,7 @@
 
 #include <stdint.h>
 #include <stdio.h>
+#include <string.h>
 #include <atomic>
 #include <functional>
 #include <map>
@@ -33,6 +34,70 @@
 #include "../gf_layout.h"
 
 namespace gfh {
+
+/* Growable output text whose appends are inline (a slot's 32 records make
+ * a hundred or more small appends). */
+class OutBuf {
+  public:
+    size_t size() const { return n_; }
+    bool empty() const { return n_ == 0; }
+    const char *data() const { return p_.get(); }
+    void clear() { n_ = 0; }
+    void shrink(size_t n) { n_ = n < n_ ? n : n_; }
+    /* at least k writable bytes at the end; commit() what was written */
+    char *room(size_t k)
+    {
+        if (n_ + k > cap_)
+            grow(n_ + k);
+        return p_.get() + n_;
+    }
+    void commit(size_t k) { n_ += k; }
+    void append(const char *s, size_t k)
+    {
+        if (k) {
+            memcpy(room(k), s, k);
+            n_ += k;
+        }
+    }
+
+  private:
+    void grow(size_t need)
+    {
+        size_t c = cap_ ? cap_ : 4096;
+        while (c < need)
+            c *= 2;
+        std::unique_ptr<char[]> q(new char[c]);
+        if (n_)
+            memcpy(q.get(), p_.get(), n_);
+        p_ = std::move(q);
+        cap_ = c;
+    }
+    std::unique_ptr<char[]> p_;
+    size_t n_ = 0, cap_ = 0;
+};
+
+/* A printf format cut once into literal runs and conversions, so the
+ * records of a slot (up to 32 with one format) do not parse it again. */
+struct FmtConv {
+    uint32_t lit_off = 0, lit_len = 0;   /* the literal text before it, in FmtPlan::lits */
+    char conv = 0;                        /* 0: the format ends after the literal        */
+    char len[3] = {0, 0, 0};              /* length modifier                             */
+    int prec = -1;                        /* -1: none given                              */
+    bool plain = false;                   /* no flags, width or '*'                      */
+    bool star_w = false, star_p = false;
+    bool bad = false;                     /* conversion too long: the call fails here    */
+    std::string spec;                     /* the whole conversion, for snprintf          */
+};
+struct FmtPlan {
+    std::string lits;
+    std::vector<FmtConv> convs;
+};
+FmtPlan compile_fmt(const char *fmt);
+
+struct FmtEntry {
+    std::string text;
+    FmtPlan plan;
+};
 
 struct Segment {
     uint8_t *slots = nullptr;       /* host address of slot 0                        */
@@ -50,11 +115,11 @@ struct Segment {
     std::vector<uint64_t> expect;   /* next ticket each slot will carry               */
     std::vector<uint32_t> cursor;   /* per server thread: slot to start the next scan */
     std::vector<uint32_t> passes;   /* per server thread: scans so far                */
-    std::unordered_map<uint64_t, std::string> fmt_cache;   /* fmt_key -> format (never overwritten) */
+    std::unordered_map<uint64_t, FmtEntry> fmt_cache;      /* fmt_key -> format (never overwritten) */
     std::mutex fmt_mu;
-    /* per server thread: fmt_key -> the string in fmt_cache, so a thread
+    /* per server thread: fmt_key -> the entry in fmt_cache, so a thread
      * takes the shared lock only for a format it has not seen */
-    std::vector<std::unordered_map<uint64_t, const std::string *>> fmt_local;
+    std::vector<std::unordered_map<uint64_t, const FmtEntry *>> fmt_local;
     void reset(uint32_t nthreads);
 };
 
@@ -111,9 +176,9 @@ class Server {
 
   private:
     int poll_active(Segment &seg, uint32_t tid, uint32_t nthreads);
-    int64_t do_printf(const char *fmt, const uint8_t *rec, std::string &out, uint64_t *stream);
+    int64_t do_printf(const FmtPlan &plan, const uint8_t *rec, OutBuf &out, uint64_t *stream);
     FILE *file_of(uint64_t h);
-    void emit(uint64_t stream, const std::string &s);
+    void emit(uint64_t stream, const char *s, size_t n);
 
     FILE *out_ = stdout;
     std::mutex out_mu_;
