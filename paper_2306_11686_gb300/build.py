@@ -30,7 +30,7 @@ CU = ["runtime.cu", "noalloc.cu", "peak.cu", "programs/legacy.cu", "programs/pro
 CPP = ["host/server.cpp", "host/mlp.cpp"]
 HEADERS = ["gf_layout.h", "gf_device.cuh", "gf_device_rpc.cuh", "gf_device_heap.cuh", "gf_program.h",
            "host/server.h", "host/range_alloc.h", "gf_errors.h", "gf_internal.h", "gf_fastdiv.cuh", "gf_paper_alloc.cuh", "gf_device_libc.cuh",
-           "gf_intpipe.cuh", "gf_strtod_fast.h", "host/fmt_fast.h"]
+           "gf_intpipe.cuh", "gf_strtod_fast.h", "host/fmt_fast.h", "host/dtoa_fixed.h"]
 
 
 def _newer(obj, deps):

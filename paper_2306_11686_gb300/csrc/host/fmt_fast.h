@@ -10,6 +10,9 @@
  * snprintf.  glibc's printf converts doubles with multi-precision
  * arithmetic; to_chars (Ryu-printf in libstdc++) is several times faster,
  * which matters when one device warp ships 32 formatted calls per slot.
+ * Doubles at precisions up to 17 digits first try dtoa::format
+ * (dtoa_fixed.h), a 128-bit table-driven conversion that is faster again
+ * and declines the cases it cannot decide exactly.
  */
 #ifndef GF_FMT_FAST_H
 #define GF_FMT_FAST_H
@@ -18,6 +21,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+
+#include "dtoa_fixed.h"
 
 namespace gfh {
 
@@ -79,6 +84,15 @@ inline bool fmt_fast(char conv, const char *len, int prec, uint64_t w, bool is_f
         const int p = prec < 0 ? 6 : prec;
         if (!std::isfinite(d) || (conv == 'g' && p == 0))
             return false;
+        if (cap >= 64) {                        /* the fixed-precision path, exact or declined */
+            uint64_t bits;
+            memcpy(&bits, &d, 8);
+            const int k = dtoa::format(conv, p, bits, buf);
+            if (k > 0) {
+                *n = k;
+                return true;
+            }
+        }
         const std::chars_format f = conv == 'e' ? std::chars_format::scientific
                                     : conv == 'f' ? std::chars_format::fixed
                                                   : std::chars_format::general;

@@ -4,6 +4,7 @@
  * Prints "fmt checked N fast F mismatches M". */
 #include <cfloat>
 #include <climits>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <random>
@@ -31,7 +32,9 @@ int main()
         {"%f", 'f', "", -1, 1},     {"%.0f", 'f', "", 0, 1},    {"%.3f", 'f', "", 3, 1},    {"%.10f", 'f', "", 10, 1},
         {"%lf", 'f', "l", -1, 1},   {"%g", 'g', "", -1, 1},     {"%.1g", 'g', "", 1, 1},    {"%.3g", 'g', "", 3, 1},
         {"%.6g", 'g', "", 6, 1},    {"%.15g", 'g', "", 15, 1},  {"%.17g", 'g', "", 17, 1},  {"%.25g", 'g', "", 25, 1},
-        {"%lg", 'g', "l", -1, 1},
+        {"%lg", 'g', "l", -1, 1},   {"%.1e", 'e', "", 1, 1},    {"%.16e", 'e', "", 16, 1},  {"%.9e", 'e', "", 9, 1},
+        {"%.1f", 'f', "", 1, 1},    {"%.2f", 'f', "", 2, 1},    {"%.6f", 'f', "", 6, 1},    {"%.17f", 'f', "", 17, 1},
+        {"%.2g", 'g', "", 2, 1},    {"%.12g", 'g', "", 12, 1},  {"%.16g", 'g', "", 16, 1},
     };
     std::mt19937_64 rng(7);
     std::vector<uint64_t> words = {0, 1, 2, 9, 10, 15, 16, 255, 256, 65535, 65536, 0x7fffffffull, 0x80000000ull,
@@ -51,6 +54,32 @@ int main()
         memcpy(&d, &b, 8);
         dbls.push_back(d);
         dbls.push_back((double)(int64_t)(rng() % 2000001) / 1000.0 - 1000.0);   /* short decimals, ties for %.0f */
+    }
+    /* near powers of ten and the decimal carries they invite */
+    for (int k = -320; k <= 308; k++) {
+        const double p = std::pow(10.0, k);
+        if (!(p > 0) || !std::isfinite(p))
+            continue;
+        double q = p;
+        for (int j = 0; j < 4; j++) {
+            dbls.push_back(q);
+            q = std::nextafter(q, 0.0);
+        }
+        q = p;
+        for (int j = 0; j < 4; j++) {
+            q = std::nextafter(q, INFINITY);
+            dbls.push_back(q);
+        }
+        dbls.push_back(p * 9.5);
+        dbls.push_back(p * 9.95);
+        dbls.push_back(p * 9.9999999999999995);
+        dbls.push_back(p * 0.99999999999999999);
+    }
+    /* integers up to 2^64, exact halves at every scale, short decimals */
+    for (int k = 0; k < 20000; k++) {
+        dbls.push_back((double)(rng() >> (rng() % 64)));
+        dbls.push_back(std::ldexp((double)(2 * (rng() % 1000000) + 1), -(int)(rng() % 60)));
+        dbls.push_back((double)(int64_t)(rng() % 200000001) / 1e6);
     }
     long n = 0, fast = 0, bad = 0;
     char a[1024], b[1024];
@@ -83,6 +112,32 @@ int main()
             }
         }
     }
+    /* the fixed-precision path alone: whatever it accepts must match */
+    long dn = 0, dacc = 0;
+    const int precs[] = {0, 1, 2, 3, 5, 6, 9, 12, 15, 16, 17};
+    const char convs[] = {'e', 'f', 'g'};
+    for (const char c : convs)
+        for (const int p : precs)
+            for (const double d : dbls) {
+                if (!std::isfinite(d))
+                    continue;
+                char f[16];
+                snprintf(f, sizeof f, "%%.%d%c", p, c);
+                const int want_n = snprintf(a, sizeof a, f, d);
+                uint64_t bits;
+                memcpy(&bits, &d, 8);
+                const int got_n = gfh::dtoa::format(c, p, bits, b);
+                dn++;
+                if (got_n <= 0)
+                    continue;
+                dacc++;
+                if (got_n != want_n || memcmp(a, b, (size_t)got_n) != 0) {
+                    if (bad < 20)
+                        printf("dtoa mismatch %s of %a: want [%.*s] got [%.*s]\n", f, d, want_n, a, got_n, b);
+                    bad++;
+                }
+            }
+    printf("dtoa checked %ld accepted %ld\n", dn, dacc);
     printf("fmt checked %ld fast %ld mismatches %ld\n", n, fast, bad);
     return 0;
 }
