@@ -2,6 +2,7 @@
 #include "server.h"
 #include "fmt_fast.h"
 
+#include <errno.h>
 #include <fcntl.h>
 #include <stdlib.h>
 #include <string.h>
@@ -204,6 +205,137 @@ extern "C" __attribute__((visibility("default"))) int gf_rec_arg(const void *rec
     if (off)
         *off = ref ? r.ptr_off((uint32_t)k) : 0;
     return 0;
+}
+
+class AsyncFile {
+  public:
+    explicit AsyncFile(int fd) : fd_(fd), th_([this] { loop(); }) {}
+    ~AsyncFile()
+    {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        th_.join();
+        if (fd_ >= 0)
+            ::close(fd_);
+    }
+    ssize_t put(const char *p, size_t n)
+    {
+        std::unique_lock<std::mutex> lk(mu_);
+        /* bounded queue: a writer far behind holds the printing threads back */
+        space_.wait(lk, [&] { return q_.size() < LIMIT || err_; });
+        if (err_)
+            return -1;
+        q_.insert(q_.end(), p, p + n);
+        if (q_.size() >= CHUNK && !busy_)  /* wake the writer for whole chunks only */
+            cv_.notify_one();
+        return (ssize_t)n;
+    }
+    int drain()
+    {
+        std::unique_lock<std::mutex> lk(mu_);
+        drain_++;
+        cv_.notify_one();
+        idle_.wait(lk, [&] { return (q_.empty() && !busy_) || err_; });
+        drain_--;
+        return err_ ? -1 : 0;
+    }
+    FILE *f = nullptr;
+
+  private:
+    void loop()
+    {
+        std::vector<char> buf;
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                /* large writes: wait for a chunk, a drain, or a short while */
+                cv_.wait_for(lk, std::chrono::milliseconds(2),
+                             [&] { return stop_ || drain_ || q_.size() >= CHUNK; });
+                if (q_.empty()) {
+                    if (stop_)
+                        return;               /* stopping with nothing queued */
+                    continue;
+                }
+                buf.swap(q_);
+                busy_ = true;
+            }
+            space_.notify_all();
+            size_t off = 0;
+            bool bad = false;
+            while (off < buf.size()) {
+                const ssize_t w = ::write(fd_, buf.data() + off, buf.size() - off);
+                if (w < 0 && errno == EINTR)
+                    continue;
+                if (w <= 0) {
+                    bad = true;
+                    break;
+                }
+                off += (size_t)w;
+            }
+            buf.clear();
+            {
+                std::lock_guard<std::mutex> g(mu_);
+                busy_ = false;
+                if (bad)
+                    err_ = true;
+            }
+            idle_.notify_all();
+            space_.notify_all();
+        }
+    }
+    static const size_t LIMIT = 64u << 20, CHUNK = 1u << 20;
+    int drain_ = 0;
+    int fd_;
+    std::mutex mu_;
+    std::condition_variable cv_, idle_, space_;
+    std::vector<char> q_;
+    bool stop_ = false, busy_ = false, err_ = false;
+    std::thread th_;
+};
+
+static ssize_t async_write_fn(void *cookie, const char *p, size_t n) { return ((AsyncFile *)cookie)->put(p, n); }
+
+AsyncFile *async_open(const char *path)
+{
+    const int fd = ::open(path, O_WRONLY | O_CREAT | O_TRUNC | O_CLOEXEC, 0666);
+    if (fd < 0)
+        return nullptr;
+    AsyncFile *a = new AsyncFile(fd);
+    cookie_io_functions_t io = {};
+    io.write = async_write_fn;
+    a->f = fopencookie(a, "w", io);
+    if (!a->f) {
+        delete a;
+        return nullptr;
+    }
+    setvbuf(a->f, nullptr, _IONBF, 0);
+    return a;
+}
+
+FILE *async_stream(AsyncFile *a) { return a ? a->f : nullptr; }
+
+int async_drain(AsyncFile *a)
+{
+    if (!a)
+        return -1;
+    if (a->f)
+        fflush(a->f);
+    return a->drain();
+}
+
+int async_close(AsyncFile *a)
+{
+    if (!a)
+        return -1;
+    int rc = a->f ? fclose(a->f) : 0;         /* nothing is buffered in the stream itself */
+    a->f = nullptr;
+    if (a->drain() != 0)
+        rc = -1;
+    delete a;
+    return rc;
 }
 
 Server::Server() {}

@@ -153,6 +153,18 @@ struct HostStats {
 
 class CopyPool;
 
+/* A stdio stream whose bytes a thread of its own writes to the file: a write
+ * through the stream only queues the bytes (the stream is unbuffered, so
+ * they are queued in call order), and the threads that print never wait for
+ * the kernel's write of the file, which is serial per file.  async_drain
+ * waits until everything queued is in the file (0, or -1 after a failed
+ * write); async_close closes the stream, drains and frees. */
+class AsyncFile;
+AsyncFile *async_open(const char *path);      /* nullptr if the file cannot be opened */
+FILE *async_stream(AsyncFile *a);
+int async_drain(AsyncFile *a);
+int async_close(AsyncFile *a);
+
 class Server {
   public:
     Server();

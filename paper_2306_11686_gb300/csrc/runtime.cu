@@ -154,6 +154,7 @@ struct gf_ctx {
     size_t intern_used = 0;
     FILE *out = stdout;
     bool own_out = false;
+    gfh::AsyncFile *aout = nullptr;   /* the stdout file, written by its own thread */
     std::mutex stats_mu;
     gf_stats last;
 };
@@ -380,8 +381,12 @@ extern "C" GF_API int gf_finalize(gf_ctx *c)
     for (auto &t : c->threads)
         t.join();
     c->server.close_all();
-    if (c->own_out && c->out)
-        fclose(c->out);
+    if (c->own_out && c->out) {
+        if (c->aout)
+            gfh::async_close(c->aout);
+        else
+            fclose(c->out);
+    }
     for (Instance *in : c->inst) {
         inst_free(in);
         delete in;
@@ -502,10 +507,10 @@ extern "C" GF_API int gf_init(const gf_config *cfg, gf_ctx **out)
             return fail(rc);
     }
     if (cf.stdout_path) {
-        c->out = fopen(cf.stdout_path, "w");
+        c->aout = gfh::async_open(cf.stdout_path);
+        c->out = gfh::async_stream(c->aout);
         if (!c->out)
             return fail(GF_EINVAL);
-        setvbuf(c->out, nullptr, _IOFBF, 4 << 20);
         c->own_out = true;
     }
     c->server.set_stdout(c->out);
@@ -981,7 +986,9 @@ extern "C" GF_API int gf_wait(gf_handle *h, int *exit_code, int64_t timeout_ns)
         rc = in->h_final.error;
     if (exit_code)
         *exit_code = in->h_final.exit_code;
-    if (c->out)
+    if (c->aout)
+        gfh::async_drain(c->aout);           /* the program's text is in the file when it is done */
+    else if (c->out)
         fflush(c->out);
     inst_release(c, in);
     delete h;

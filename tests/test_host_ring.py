@@ -27,3 +27,15 @@ def test_ring_scenario(ring_bin, tmp_path, scenario):
     p = subprocess.run([ring_bin, scenario, str(tmp_path / "out.txt")], capture_output=True, text=True, timeout=120)
     assert p.returncode == 0, p.stdout + p.stderr
     assert p.stdout.strip().endswith("OK " + scenario)
+
+
+def test_async_output_file(tmp_path):
+    """The stdout file written by its own thread: lines from four threads
+    (some of 65 KB, in several writes) are whole and in per-thread order
+    after every drain and after close."""
+    exe = str(tmp_path / "async_check")
+    subprocess.run(["g++", "-std=c++17", "-O2", "-pthread", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+                    os.path.join(ROOT, "tests", "host", "async_file_check.cpp"),
+                    os.path.join(CSRC, "host", "server.cpp"), "-o", exe], check=True)
+    p = subprocess.run([exe, str(tmp_path / "out.txt")], capture_output=True, text=True, timeout=120)
+    assert p.returncode == 0 and "OK" in p.stdout, p.stdout + p.stderr
