@@ -54,8 +54,8 @@ RecView::RecView(const uint8_t *r) : base(r)
 /*
  * Copy threads kept for the server's life.  A large write hands every thread
  * one slice of the range and waits: creating and joining a dozen threads for
- * every 32 MiB chunk cost more than the copy itself.  One job at a time (the
- * server's output lock already serialises large writes).
+ * every 32 MiB chunk cost more than the copy itself.  One job at a time
+ * (pool_mu_; large writes to different files take turns).
  */
 class CopyPool {
   public:
@@ -173,6 +173,7 @@ size_t Server::big_fwrite(const void *src, size_t size, size_t nmemb, FILE *f)
         close(rfd);
         return bad ? 0 : fwrite(src, size, nmemb, f);
     }
+    std::lock_guard<std::mutex> g(pool_mu_);
     if (!pool_)
         pool_.reset(new CopyPool());
     pool_->copy((unsigned char *)m + (pos - mstart), (const unsigned char *)src, n);
@@ -338,10 +339,10 @@ int async_close(AsyncFile *a)
     return rc;
 }
 
-Server::Server() {}
+Server::Server() : out_s_(std::make_shared<Stream>(stdout)), err_s_(std::make_shared<Stream>(stderr)) {}
 Server::~Server() { close_all(); }
 
-void Server::set_stdout(FILE *f) { out_ = f ? f : stdout; }
+void Server::set_stdout(FILE *f) { out_s_ = std::make_shared<Stream>(f ? f : stdout); }
 void Server::set_dma(d2h_fn d2h, h2d_fn h2d)
 {
     d2h_ = d2h;
@@ -356,33 +357,45 @@ int Server::register_user(uint32_t opcode, user_fn fn, void *user)
 
 void Server::close_all()
 {
-    std::lock_guard<std::mutex> g(files_mu_);
-    for (uint64_t h : files_)
-        fclose((FILE *)(uintptr_t)h);
-    files_.clear();
-    std::lock_guard<std::mutex> g2(out_mu_);
-    fflush(out_);
+    std::unordered_map<uint64_t, std::shared_ptr<Stream>> open;
+    {
+        std::lock_guard<std::mutex> g(files_mu_);
+        open.swap(files_);
+    }
+    for (auto &kv : open) {
+        std::lock_guard<std::mutex> g(kv.second->mu);
+        if (!kv.second->closed) {
+            kv.second->closed = true;
+            fclose(kv.second->f);
+        }
+    }
+    if (out_s_) {
+        std::lock_guard<std::mutex> g(out_s_->mu);
+        fflush(out_s_->f);
+    }
 }
 
-FILE *Server::file_of(uint64_t h)
+std::shared_ptr<Server::Stream> Server::stream_of(uint64_t h)
 {
     if (h == GF_STDOUT_H)
-        return out_;
+        return out_s_;
     if (h == GF_STDERR_H)
-        return stderr;
+        return err_s_;
     std::lock_guard<std::mutex> g(files_mu_);
-    return files_.count(h) ? (FILE *)(uintptr_t)h : nullptr;
+    auto it = files_.find(h);
+    return it == files_.end() ? nullptr : it->second;
 }
 
 void Server::emit(uint64_t stream, const char *s, size_t n)
 {
     if (!n)
         return;
-    FILE *f = file_of(stream);
-    if (!f)
+    const std::shared_ptr<Stream> st = stream_of(stream);
+    if (!st)
         return;
-    std::lock_guard<std::mutex> g(out_mu_);
-    fwrite(s, 1, n, f);
+    std::lock_guard<std::mutex> g(st->mu);
+    if (!st->closed)
+        fwrite(s, 1, n, st->f);
 }
 
 /*
@@ -612,7 +625,7 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
         uint64_t stream = 0;
         int64_t n = do_printf(compile_fmt(fmt), rec, s, &stream);
         if (n >= 0) {
-            if (!file_of(stream))
+            if (!stream_of(stream))
                 return -1;
             emit(stream, s.data(), s.size());
         }
@@ -625,27 +638,36 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
         if (!f)
             return 0;
         std::lock_guard<std::mutex> g(files_mu_);
-        files_.insert((uint64_t)(uintptr_t)f);
+        files_[(uint64_t)(uintptr_t)f] = std::make_shared<Stream>(f);
         return (int64_t)(uintptr_t)f;
     }
     case GF_OP_FCLOSE: {
         if (r.nargs < 1)
             return -1;
         const uint64_t h = r.word(0);
-        std::lock_guard<std::mutex> g(files_mu_);
-        if (!files_.count(h))
+        std::shared_ptr<Stream> st;
+        {
+            std::lock_guard<std::mutex> g(files_mu_);
+            auto it = files_.find(h);
+            if (it == files_.end())
+                return -1;
+            st = it->second;
+            files_.erase(it);
+        }
+        std::lock_guard<std::mutex> g(st->mu);   /* after the stream's pending writes */
+        if (st->closed)
             return -1;
-        files_.erase(h);
-        return fclose((FILE *)(uintptr_t)h);
+        st->closed = true;
+        return fclose(st->f);
     }
     case GF_OP_FFLUSH: {
         if (r.nargs < 1)
             return -1;
-        FILE *f = file_of(r.word(0));
-        if (!f)
+        const std::shared_ptr<Stream> st = stream_of(r.word(0));
+        if (!st)
             return -1;
-        std::lock_guard<std::mutex> g(out_mu_);
-        return fflush(f);
+        std::lock_guard<std::mutex> g(st->mu);
+        return st->closed ? -1 : fflush(st->f);
     }
     case GF_OP_FWRITE:
     case GF_OP_FREAD: {
@@ -653,9 +675,13 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
         if (r.nargs < 4)
             return 0;
         const uint64_t size = r.word(0), nmemb = r.word(1);
-        FILE *f = file_of(r.word(2));
-        if (!f || size == 0)
+        const std::shared_ptr<Stream> st = stream_of(r.word(2));
+        if (!st || size == 0)
             return 0;
+        std::lock_guard<std::mutex> g(st->mu);   /* the whole transfer, DMA included */
+        if (st->closed)
+            return 0;
+        FILE *f = st->f;
         const uint64_t bytes = size * nmemb;
         if (r.tag(3) == GF_T_ARENA) {
             /* staged in the bulk arena by the device grid (fwrite) or to be
@@ -664,7 +690,6 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
             const uint64_t len = r.nargs > 4 ? r.word(4) : 0;
             if (!seg || !seg->bulk || off + len > seg->bulk_bytes || len < bytes)
                 return 0;
-            std::lock_guard<std::mutex> g(out_mu_);
             const size_t k = op == GF_OP_FWRITE ? big_fwrite(seg->bulk + off, size, nmemb, f)
                                                 : fread(seg->bulk + off, size, nmemb, f);
             stats.dma_bytes += k * size;
@@ -674,12 +699,10 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
             uint8_t *b = r.blob(3);
             if (r.blob_len(3) < bytes)
                 return 0;
-            std::lock_guard<std::mutex> g(out_mu_);
             return op == GF_OP_FWRITE ? (int64_t)fwrite(b, size, nmemb, f) : (int64_t)fread(b, size, nmemb, f);
         }
         const uint64_t dev = r.word(3);
         uint64_t done = 0;
-        std::lock_guard<std::mutex> g(out_mu_);
         if (op == GF_OP_FWRITE) {
             if (!d2h_)
                 return 0;
@@ -880,7 +903,7 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
                 }
                 pay += rh->bytes;
             }
-            if (!first && !file_of(stream)) {
+            if (!first && !stream_of(stream)) {
                 bad_stream = true;
                 out.shrink(mark);
             }

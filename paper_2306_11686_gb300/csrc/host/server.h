@@ -189,13 +189,22 @@ class Server {
   private:
     int poll_active(Segment &seg, uint32_t tid, uint32_t nthreads);
     int64_t do_printf(const FmtPlan &plan, const uint8_t *rec, OutBuf &out, uint64_t *stream);
-    FILE *file_of(uint64_t h);
+    /* A stream the device can name: stdout, stderr, or a FILE it opened.
+     * Each has its own lock, which orders that stream's writes, reads,
+     * flushes and close; different streams proceed in parallel. */
+    struct Stream {
+        explicit Stream(FILE *x) : f(x) {}
+        FILE *f;
+        std::mutex mu;
+        bool closed = false;
+    };
+    std::shared_ptr<Stream> stream_of(uint64_t h);
     void emit(uint64_t stream, const char *s, size_t n);
 
-    FILE *out_ = stdout;
-    std::mutex out_mu_;
+    std::shared_ptr<Stream> out_s_, err_s_;
     std::mutex files_mu_;
-    std::set<uint64_t> files_;
+    std::unordered_map<uint64_t, std::shared_ptr<Stream>> files_;
+    std::mutex pool_mu_;                 /* one large write through the copy pool at a time */
     d2h_fn d2h_;
     h2d_fn h2d_;
     region_fn region_;
