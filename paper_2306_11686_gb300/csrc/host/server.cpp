@@ -375,22 +375,34 @@ void Server::close_all()
     }
 }
 
-std::shared_ptr<Server::Stream> Server::stream_of(uint64_t h)
+Server::Stream *Server::stream_of(uint64_t h, std::shared_ptr<Stream> &hold)
 {
     if (h == GF_STDOUT_H)
-        return out_s_;
+        return out_s_.get();
     if (h == GF_STDERR_H)
-        return err_s_;
+        return err_s_.get();
     std::lock_guard<std::mutex> g(files_mu_);
     auto it = files_.find(h);
-    return it == files_.end() ? nullptr : it->second;
+    if (it == files_.end())
+        return nullptr;
+    hold = it->second;
+    return hold.get();
+}
+
+bool Server::stream_valid(uint64_t h)
+{
+    if (h == GF_STDOUT_H || h == GF_STDERR_H)
+        return true;
+    std::lock_guard<std::mutex> g(files_mu_);
+    return files_.count(h) != 0;
 }
 
 void Server::emit(uint64_t stream, const char *s, size_t n)
 {
     if (!n)
         return;
-    const std::shared_ptr<Stream> st = stream_of(stream);
+    std::shared_ptr<Stream> hold;
+    Stream *st = stream_of(stream, hold);
     if (!st)
         return;
     std::lock_guard<std::mutex> g(st->mu);
@@ -625,7 +637,7 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
         uint64_t stream = 0;
         int64_t n = do_printf(compile_fmt(fmt), rec, s, &stream);
         if (n >= 0) {
-            if (!stream_of(stream))
+            if (!stream_valid(stream))
                 return -1;
             emit(stream, s.data(), s.size());
         }
@@ -663,7 +675,8 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
     case GF_OP_FFLUSH: {
         if (r.nargs < 1)
             return -1;
-        const std::shared_ptr<Stream> st = stream_of(r.word(0));
+        std::shared_ptr<Stream> hold;
+        Stream *st = stream_of(r.word(0), hold);
         if (!st)
             return -1;
         std::lock_guard<std::mutex> g(st->mu);
@@ -675,7 +688,8 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
         if (r.nargs < 4)
             return 0;
         const uint64_t size = r.word(0), nmemb = r.word(1);
-        const std::shared_ptr<Stream> st = stream_of(r.word(2));
+        std::shared_ptr<Stream> hold;
+        Stream *st = stream_of(r.word(2), hold);
         if (!st || size == 0)
             return 0;
         std::lock_guard<std::mutex> g(st->mu);   /* the whole transfer, DMA included */
@@ -903,7 +917,7 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
                 }
                 pay += rh->bytes;
             }
-            if (!first && !stream_of(stream)) {
+            if (!first && !stream_valid(stream)) {
                 bad_stream = true;
                 out.shrink(mark);
             }

@@ -198,7 +198,11 @@ class Server {
         std::mutex mu;
         bool closed = false;
     };
-    std::shared_ptr<Stream> stream_of(uint64_t h);
+    /* the stream named h, or nullptr; a FILE the device opened is kept alive
+     * through `hold` (stdout and stderr live as long as the server and are
+     * returned without touching a shared count) */
+    Stream *stream_of(uint64_t h, std::shared_ptr<Stream> &hold);
+    bool stream_valid(uint64_t h);
     void emit(uint64_t stream, const char *s, size_t n);
 
     std::shared_ptr<Stream> out_s_, err_s_;
