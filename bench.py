@@ -241,6 +241,9 @@ def main():
     ap.add_argument("--kseg", type=int, default=None,
                     help="run each sweep as columns of K planes per parallel iteration (0 = one iteration per "
                          "point; the program's default when omitted)")
+    ap.add_argument("--server-threads", type=int, default=None,
+                    help="host server threads for --workload serve and stress (a power of two; the "
+                         "workload's default when omitted)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the same-process extra measurements (printf calls/s with and without warp "
@@ -372,7 +375,7 @@ def main():
                                      "through the plain runtime (24 B per iteration, 6.4 GB)",
                          "GBps": round(ax["GBps"], 1), "frac": round(ax["GBps"] / peak, 4),
                          "peak": peak, "peak_kind": peak_kind, "correct": ax["correct"]},
-                 "stress": measure.printf_rate(1 << 20, out_dir=out_dir, server_threads=8)}
+                 "stress": measure.printf_rate(1 << 20, out_dir=out_dir, server_threads=16)}
     cpu = cpu_omp = None
     if rank == 0 and args.cpu_sweeps > 0:
         cv, cdt, cc, pinned = cpu_oracle_sample(N, args.cpu_sweeps, tmp)

@@ -84,6 +84,7 @@ def printf_rate(T=1 << 20, out_dir=None, server_threads=4):
 def stress(args):
     import torch
     T = 1 << 20
+    nthr = getattr(args, "server_threads", None) or 4
     tmp = tempfile.mkdtemp(prefix="gfstress", dir=_out_dir(args))
     sizes = torch.from_numpy(inputs.loguniform_int(3, 8 * T, 16, 65536).astype(np.int32)).cuda()
     cs = torch.zeros(T, dtype=torch.int64, device="cuda")
@@ -91,7 +92,7 @@ def stress(args):
     stream = torch.cuda.Stream()
     out = {}
     for agg in (1, 0):
-        with gf.Context(aggregate=agg, stream=stream, heap_bytes=8 << 30, heap_small_pct=95, server_threads=4,
+        with gf.Context(aggregate=agg, stream=stream, heap_bytes=8 << 30, heap_small_pct=95, server_threads=nthr,
                         stdout_path=os.path.join(tmp, "out.txt"), timeout_ns=int(120e9)) as ctx:
             _timed_run(ctx, stream, "printf_only", [1 << 14], [])          # warm-up
             b0 = ctx.stats().host_ring_bytes
@@ -110,7 +111,7 @@ def stress(args):
                 sst = ctx.stats()
     line = {"metric": "RPC calls/s + p99 latency", "value": round(out[1]["calls_per_s"]), "unit": "calls/s",
             "n_gpus": 1, "higher_is_better": True, "dtype": "int/bytes", "data": "synthetic",
-            "config": {"workload": "2^20 iterations x 4 printf (int/double formats), host server 4 threads",
+            "config": {"workload": f"2^20 iterations x 4 printf (int/double formats), host server {nthr} threads",
                        "output": os.path.dirname(tmp)},
             "detail": {"aggregated": out[1], "per_thread": out[0],
                        "aggregation_speedup": out[1]["calls_per_s"] / out[0]["calls_per_s"],
@@ -221,6 +222,10 @@ def learned(args):
 SERVE_THREADS = 4
 
 
+def _serve_threads(args):
+    return getattr(args, "server_threads", None) or SERVE_THREADS
+
+
 def _spmv_alone(serve, n, P, tmp, fp64_peak=None):
     """The served SpMV without its libc requests: P programs at once (16
     instances), device time of the whole set (first start to last end)."""
@@ -259,20 +264,20 @@ def serve_run(args):
     runs = []
     for _ in range(3):                  # the median of three runs (a run varies by about 10%)
         recs, agg = serve.serve(progs, outs, max_concurrent=16, rate_hz=400.0, heap_bytes=1 << 30, ring_slots=1024,
-                                server_threads=SERVE_THREADS, stdout_path=os.path.join(tmp, "out.txt"))
+                                server_threads=_serve_threads(args), stdout_path=os.path.join(tmp, "out.txt"))
         agg["errors"] = sum(1 for r in recs if r["rc"] or r["exit"])
         runs.append(agg)
     runs.sort(key=lambda a: a["calls_per_s"])
     agg = dict(runs[1])
     agg["calls_per_s_runs"] = [round(a["calls_per_s"]) for a in runs]
     agg["errors"] = sum(a["errors"] for a in runs)
-    agg["server_threads"] = SERVE_THREADS
+    agg["server_threads"] = _serve_threads(args)
     agg["input_gen_s"] = t_gen
     # the plain single-program runtime on the same GPU: the same programs one at a time
     for pr in progs:
         pr.reset()
     recs1, one = serve.serve(progs, outs, max_concurrent=1, heap_bytes=1 << 30, ring_slots=1024,
-                             server_threads=SERVE_THREADS, stdout_path=os.path.join(tmp, "out1.txt"))
+                             server_threads=_serve_threads(args), stdout_path=os.path.join(tmp, "out1.txt"))
     agg["single_program_runtime"] = {k: one[k] for k in ("wall_s", "calls_per_s", "rpc_p50_ns_median",
                                                           "rpc_p99_ns_max", "latency_p50_s", "latency_p99_s")}
     agg["single_program_runtime"]["errors"] = sum(1 for r in recs1 if r["rc"] or r["exit"])
