@@ -642,6 +642,7 @@ static __device__ __noinline__ size_t fwrite_bulk(const void *buf, size_t size, 
         pack_all(a, 1ull, (unsigned long long)len, (unsigned long long)f);
         a.val(GF_T_ARENA, (uint64_t)k * half);
         a.val(GF_T_U64, len);
+        a.val(GF_T_U64, bytes - off);            /* the whole write still to come: the host maps it once */
         if (rpc_post1(GF_OP_FWRITE, a, &tk) != GF_OK)
             ok = false;
         else {

@@ -135,51 +135,96 @@ class CopyPool {
  * into it (page faults of different pages proceed in parallel); the stdio
  * position is then moved past the data.  The bytes in the file are the same;
  * anything that is not a plain regular file, and small writes, use fwrite.
+ *
+ * A write the device sends in chunks (the halves of its bulk arena) says in
+ * `rest` how many bytes remain including this chunk: the file is sized and
+ * the whole range mapped once, at the first chunk, and released after the
+ * last one, so the chunks cost no mapping, sizing or unmapping of their own.
+ * Anything else done to the stream in between, or its close, first settles
+ * the mapping (bulk_settle), trimming the file to what was written when the
+ * write stopped early.
  */
-size_t Server::big_fwrite(const void *src, size_t size, size_t nmemb, FILE *f)
+void Server::bulk_settle(Stream *st)
 {
+    Stream::Bulk &b = st->bulk;
+    if (!b.m)
+        return;
+    munmap(b.m, b.mlen);
+    if (b.next < b.end) {                        /* stopped early: drop the unwritten tail */
+        const int64_t keep = b.next > b.orig ? b.next : b.orig;
+        if (keep < b.end && ftruncate(b.rfd, (off_t)keep) != 0) {
+            /* the file keeps its length; nothing else to undo */
+        }
+    }
+    close(b.rfd);
+    b = Stream::Bulk();
+}
+
+size_t Server::big_fwrite(Stream *st, const void *src, size_t size, size_t nmemb, uint64_t rest)
+{
+    FILE *f = st->f;
+    Stream::Bulk &b = st->bulk;
     const uint64_t n = (uint64_t)size * nmemb;
     const uint64_t min_par = 8ull << 20;
-    if (n < min_par)
+    if (rest < n)
+        rest = n;
+    if (!b.m && rest < min_par)
         return fwrite(src, size, nmemb, f);
-    if (fflush(f) != 0)
+    if (fflush(f) != 0) {
+        bulk_settle(st);
         return 0;
-    const int fd = fileno(f);
-    struct stat sb;
+    }
     const off_t pos = ftello(f);
-    const int fl = fd >= 0 ? fcntl(fd, F_GETFL) : -1;
-    const bool writable = fl >= 0 && ((fl & O_ACCMODE) == O_WRONLY || (fl & O_ACCMODE) == O_RDWR);
-    if (fd < 0 || pos < 0 || !writable || (fl & O_APPEND) || fstat(fd, &sb) != 0 || !S_ISREG(sb.st_mode) ||
-        lseek(fd, 0, SEEK_CUR) != pos)
-        return fwrite(src, size, nmemb, f);
-    /* a shared writable mapping needs a descriptor opened for reading too:
-     * reopen the same file read-write through /proc (fall back if refused) */
-    char path[64];
-    snprintf(path, sizeof path, "/proc/self/fd/%d", fd);
-    const int rfd = open(path, O_RDWR);
-    if (rfd < 0)
-        return fwrite(src, size, nmemb, f);
-    const off_t end = pos + (off_t)n;
-    if (end > sb.st_size && ftruncate(rfd, end) != 0) {
-        close(rfd);
-        return fwrite(src, size, nmemb, f);
+    if (b.m && (pos != (off_t)b.next || (int64_t)(pos + n) > b.end))
+        bulk_settle(st);                         /* not the continuation of the mapped write */
+    if (!b.m) {
+        const int fd = fileno(f);
+        struct stat sb;
+        const int fl = fd >= 0 ? fcntl(fd, F_GETFL) : -1;
+        const bool writable = fl >= 0 && ((fl & O_ACCMODE) == O_WRONLY || (fl & O_ACCMODE) == O_RDWR);
+        if (fd < 0 || pos < 0 || !writable || (fl & O_APPEND) || fstat(fd, &sb) != 0 || !S_ISREG(sb.st_mode) ||
+            lseek(fd, 0, SEEK_CUR) != pos)
+            return fwrite(src, size, nmemb, f);
+        /* a shared writable mapping needs a descriptor opened for reading too:
+         * reopen the same file read-write through /proc (fall back if refused) */
+        char path[64];
+        snprintf(path, sizeof path, "/proc/self/fd/%d", fd);
+        const int rfd = open(path, O_RDWR | O_CLOEXEC);
+        if (rfd < 0)
+            return fwrite(src, size, nmemb, f);
+        const off_t end = pos + (off_t)rest;
+        if (end > sb.st_size && ftruncate(rfd, end) != 0) {
+            close(rfd);
+            return fwrite(src, size, nmemb, f);
+        }
+        const long pg = sysconf(_SC_PAGESIZE);
+        const off_t mstart = pos / pg * pg;
+        const size_t mlen = (size_t)(end - mstart);
+        void *m = mmap(nullptr, mlen, PROT_WRITE | PROT_READ, MAP_SHARED, rfd, mstart);
+        if (m == MAP_FAILED) {
+            const int bad = end > sb.st_size && ftruncate(rfd, sb.st_size) != 0;
+            close(rfd);
+            return bad ? 0 : fwrite(src, size, nmemb, f);
+        }
+        b.m = (uint8_t *)m;
+        b.mlen = mlen;
+        b.mstart = mstart;
+        b.next = pos;
+        b.end = end;
+        b.orig = sb.st_size;
+        b.rfd = rfd;
     }
-    const long pg = sysconf(_SC_PAGESIZE);
-    const off_t mstart = pos / pg * pg;
-    const size_t mlen = (size_t)(end - mstart);
-    void *m = mmap(nullptr, mlen, PROT_WRITE | PROT_READ, MAP_SHARED, rfd, mstart);
-    if (m == MAP_FAILED) {
-        const int bad = end > sb.st_size && ftruncate(rfd, sb.st_size) != 0;
-        close(rfd);
-        return bad ? 0 : fwrite(src, size, nmemb, f);
+    {
+        std::lock_guard<std::mutex> g(pool_mu_);
+        if (!pool_)
+            pool_.reset(new CopyPool());
+        pool_->copy(b.m + (pos - b.mstart), (const unsigned char *)src, n);
     }
-    std::lock_guard<std::mutex> g(pool_mu_);
-    if (!pool_)
-        pool_.reset(new CopyPool());
-    pool_->copy((unsigned char *)m + (pos - mstart), (const unsigned char *)src, n);
-    munmap(m, mlen);
-    close(rfd);
-    if (fseeko(f, end, SEEK_SET) != 0)
+    b.next = pos + (int64_t)n;
+    const bool last = b.next >= b.end;
+    if (last)
+        bulk_settle(st);
+    if (fseeko(f, pos + (off_t)n, SEEK_SET) != 0)
         return 0;
     return nmemb;
 }
@@ -365,6 +410,7 @@ void Server::close_all()
     for (auto &kv : open) {
         std::lock_guard<std::mutex> g(kv.second->mu);
         if (!kv.second->closed) {
+            bulk_settle(kv.second.get());
             kv.second->closed = true;
             fclose(kv.second->f);
         }
@@ -406,8 +452,10 @@ void Server::emit(uint64_t stream, const char *s, size_t n)
     if (!st)
         return;
     std::lock_guard<std::mutex> g(st->mu);
-    if (!st->closed)
+    if (!st->closed) {
+        bulk_settle(st);
         fwrite(s, 1, n, st->f);
+    }
 }
 
 /*
@@ -669,6 +717,7 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
         std::lock_guard<std::mutex> g(st->mu);   /* after the stream's pending writes */
         if (st->closed)
             return -1;
+        bulk_settle(st.get());
         st->closed = true;
         return fclose(st->f);
     }
@@ -680,7 +729,10 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
         if (!st)
             return -1;
         std::lock_guard<std::mutex> g(st->mu);
-        return st->closed ? -1 : fflush(st->f);
+        if (st->closed)
+            return -1;
+        bulk_settle(st);
+        return fflush(st->f);
     }
     case GF_OP_FWRITE:
     case GF_OP_FREAD: {
@@ -704,11 +756,16 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
             const uint64_t len = r.nargs > 4 ? r.word(4) : 0;
             if (!seg || !seg->bulk || off + len > seg->bulk_bytes || len < bytes)
                 return 0;
-            const size_t k = op == GF_OP_FWRITE ? big_fwrite(seg->bulk + off, size, nmemb, f)
+            /* bytes of the whole chunked write still to come, this chunk included */
+            const uint64_t rest = r.nargs > 5 ? r.word(5) : bytes;
+            if (op != GF_OP_FWRITE)
+                bulk_settle(st);
+            const size_t k = op == GF_OP_FWRITE ? big_fwrite(st, seg->bulk + off, size, nmemb, rest)
                                                 : fread(seg->bulk + off, size, nmemb, f);
             stats.dma_bytes += k * size;
             return (int64_t)k;
         }
+        bulk_settle(st);
         if (r.tag(3) != GF_T_DMA) {
             uint8_t *b = r.blob(3);
             if (r.blob_len(3) < bytes)

@@ -197,6 +197,14 @@ class Server {
         FILE *f;
         std::mutex mu;
         bool closed = false;
+        /* a large write in progress, arriving in chunks: the file range of
+         * the whole write, sized and mapped at its first chunk */
+        struct Bulk {
+            uint8_t *m = nullptr;
+            size_t mlen = 0;
+            int64_t mstart = 0, next = 0, end = 0, orig = 0;
+            int rfd = -1;
+        } bulk;
     };
     /* the stream named h, or nullptr; a FILE the device opened is kept alive
      * through `hold` (stdout and stderr live as long as the server and are
@@ -218,7 +226,8 @@ class Server {
     std::mutex user_mu_;
     std::map<uint32_t, std::pair<user_fn, void *>> user_;
     std::unique_ptr<CopyPool> pool_;   /* copy threads of large writes, started on first use */
-    size_t big_fwrite(const void *src, size_t size, size_t nmemb, FILE *f);
+    size_t big_fwrite(Stream *st, const void *src, size_t size, size_t nmemb, uint64_t rest);
+    void bulk_settle(Stream *st);
 };
 
 /* record accessors (shared with tests) */

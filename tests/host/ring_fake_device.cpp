@@ -16,6 +16,8 @@
  *   stall      the server pauses: producers report a timeout, then recover
  *   threads    4 server threads, per-producer order still holds
  *   fmtcache   the format ships once; later slots carry only its key
+ *   bulkfile   large fwrites from the bulk arena between small inline ones
+ *   bulkchunks large fwrites in chunks mapped once, and writes cut short
  */
 #include <stdio.h>
 #include <stdlib.h>
@@ -405,6 +407,75 @@ int main(int argc, char **argv)
                 memcmp(got.data() + pre + 4 + len, arena.data(), len) ||
                 memcmp(got.data() + pre + 4 + 2 * len, "TAIL", 4))
                 return fail(mode);
+        }
+        remove(path.c_str());
+        S.join();
+        fclose(out);
+    } else if (sc == "bulkchunks") {
+        /* large writes sent in chunks that name the bytes still to come: the
+         * file is mapped once per write; a write cut short (another call on
+         * the stream, or fclose, before its last chunk) leaves no unwritten
+         * tail in the file */
+        const uint64_t C = (9ull << 20) + 24;
+        std::vector<uint8_t> arena(C);
+        R.seg.bulk = arena.data();
+        R.seg.bulk_bytes = C;
+        auto fill = [&](int tag) {
+            for (uint64_t k = 0; k < C; k++)
+                arena[k] = (uint8_t)(((k + 977 * (uint64_t)tag) * 2654435761ull) >> 13);
+        };
+        auto chunk = [&](int64_t fh, uint64_t rest) {
+            return call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', C, ""}, {'L', (uint64_t)fh, ""}, {'A', 0, ""},
+                                           {'L', C, ""}, {'L', rest, ""}}) == (int64_t)C;
+        };
+        const std::string path = std::string(argv[2]) + ".bin";
+        for (const char *mode : {"wb", "w+b", "ab"}) {
+            std::string want;
+            if (!strcmp(mode, "ab")) {
+                FILE *pre = fopen(path.c_str(), "wb");
+                fwrite("PRE", 1, 3, pre);
+                fclose(pre);
+                want = "PRE";
+            }
+            const int64_t fh = call1(R, GF_OP_FOPEN, {{'s', 0, path + '\0'}, {'s', 0, std::string(mode) + '\0'}});
+            if (!fh)
+                return fail("fopen");
+            auto inl = [&](const char *t) {
+                want += t;
+                return call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', 4, ""}, {'L', (uint64_t)fh, ""},
+                                               {'b', 0, std::string(t, 4)}}) == 4;
+            };
+            if (!inl("HEAD"))
+                return fail("inline fwrite");
+            for (int c = 0; c < 3; c++) {               /* a whole write in three chunks */
+                fill(c);
+                want.append((const char *)arena.data(), C);
+                if (!chunk(fh, (3 - c) * C))
+                    return fail("chunk");
+            }
+            for (int c = 0; c < 2; c++) {               /* a write of three chunks cut after two */
+                fill(10 + c);
+                want.append((const char *)arena.data(), C);
+                if (!chunk(fh, (3 - c) * C))
+                    return fail("chunk of the cut write");
+            }
+            if (!inl("MID!") || !inl("TAIL"))
+                return fail("inline fwrite after");
+            fill(20);                                   /* cut again, then closed */
+            want.append((const char *)arena.data(), C);
+            if (!chunk(fh, 2 * C))
+                return fail("chunk before fclose");
+            if (call1(R, GF_OP_FCLOSE, {{'L', (uint64_t)fh, ""}}) != 0)
+                return fail("fclose");
+            FILE *in = fopen(path.c_str(), "rb");
+            std::string got(want.size() + 64, '\0');
+            const size_t k = fread(&got[0], 1, got.size(), in);
+            fclose(in);
+            got.resize(k);
+            if (got != want) {
+                printf("%s: %zu bytes, want %zu\n", mode, got.size(), want.size());
+                return fail(mode);
+            }
         }
         remove(path.c_str());
         S.join();
