@@ -26,7 +26,8 @@
  *    other stacks of their SM, then of the other SMs, before failing;
  *  - sizes above 64 KiB take 64 KiB pages first-fit from a sorted extent list
  *    under one device lock (rare; the paper notes large serial-part
- *    allocations come from the initial thread, Sec. 3.4).
+ *    allocations come from the initial thread, Sec. 3.4); the last freed
+ *    large block waits in a one-entry cache for a request of its size.
  *
  * Out of memory returns NULL.  Blocks are 16-byte aligned.  Freeing a pointer
  * that the heap did not hand out is counted in n_bad_free and ignored.
@@ -277,25 +278,15 @@ static __device__ void *large_alloc(gf_heap *H, uint64_t n, int64_t timeout_ns)
     return r;
 }
 
-static __device__ bool large_free(gf_heap *H, uint64_t addr, int64_t timeout_ns)
+/* pages [pg, pg + np) back into the sorted extent table, merged with the
+ * free extents around them (each read from the table once: the lock holder
+ * is the only writer, so the copies stay current) */
+static __device__ bool large_insert(gf_heap *H, uint32_t pg, uint32_t np, int64_t timeout_ns)
 {
-    const uint64_t off = addr - H->large_base;
-    if (off & ((1ull << GF_PAGE_SHIFT) - 1))
-        return false;
-    const uint32_t pg = (uint32_t)(off >> GF_PAGE_SHIFT);
     if (!large_lock(H, timeout_ns))
         return false;
     volatile uint64_t *ext = (volatile uint64_t *)H->large_ext;
-    volatile uint32_t *sz = (volatile uint32_t *)H->large_size;
-    const uint32_t np = sz[pg];
-    if (np == 0) {
-        large_unlock(H);
-        return false;
-    }
-    sz[pg] = 0;
     uint32_t cnt = *(volatile uint32_t *)&H->large_next;
-    /* the free extents around pg, each read from the table once: the lock
-     * holder is the only writer, so the copies stay current */
     uint32_t k = 0;
     uint64_t prev = 0, cur = 0;
     for (; k < cnt; k++) {
@@ -304,13 +295,11 @@ static __device__ bool large_free(gf_heap *H, uint64_t addr, int64_t timeout_ns)
             break;
         prev = cur;
     }
-    uint32_t start = pg, len = np;
     const bool merge_prev = k > 0 && (uint32_t)prev + (uint32_t)(prev >> 32) == pg;
     const bool merge_next = k < cnt && pg + np == (uint32_t)cur;
     if (merge_prev && merge_next) {
-        start = (uint32_t)prev;
-        len = (uint32_t)(prev >> 32) + np + (uint32_t)(cur >> 32);
-        ext[k - 1] = (uint64_t)start | ((uint64_t)len << 32);
+        const uint32_t len = (uint32_t)(prev >> 32) + np + (uint32_t)(cur >> 32);
+        ext[k - 1] = (uint64_t)(uint32_t)prev | ((uint64_t)len << 32);
         for (uint32_t q = k; q + 1 < cnt; q++)
             ext[q] = ext[q + 1];
         cnt--;
@@ -329,6 +318,56 @@ static __device__ bool large_free(gf_heap *H, uint64_t addr, int64_t timeout_ns)
     return true;
 }
 
+/*
+ * The last freed large block waits in a one-entry cache (its page count in
+ * the high word) instead of going back to the extent table: a program that
+ * frees a block and then asks for one of the same size -- a scratch buffer
+ * per iteration -- gets it back with one compare-and-swap, and the free is
+ * one exchange, neither taking the lock.  A request of another size, or one
+ * the table cannot serve, first returns the cached block to the table, so
+ * first fit still sees every free page merged.
+ */
+static __device__ void *large_malloc(gf_heap *H, uint64_t n, int64_t timeout_ns)
+{
+    const uint32_t need = (uint32_t)((n + (1ull << GF_PAGE_SHIFT) - 1) >> GF_PAGE_SHIFT);
+    unsigned long long *cache = (unsigned long long *)&H->large_cache;
+    unsigned long long c = *(volatile unsigned long long *)cache;
+    if (c) {
+        if ((uint32_t)(c >> 32) == need) {
+            if (atomicCAS(cache, c, 0ull) == c) {
+                const uint32_t pg = (uint32_t)c;
+                ((volatile uint32_t *)H->large_size)[pg] = need;
+                return (void *)(H->large_base + ((uint64_t)pg << GF_PAGE_SHIFT));
+            }
+        } else if ((c = atomicExch(cache, 0ull)) != 0ull) {
+            large_insert(H, (uint32_t)c, (uint32_t)(c >> 32), timeout_ns);
+        }
+    }
+    void *p = large_alloc(H, n, timeout_ns);
+    if (!p && (c = atomicExch(cache, 0ull)) != 0ull &&
+        large_insert(H, (uint32_t)c, (uint32_t)(c >> 32), timeout_ns))
+        p = large_alloc(H, n, timeout_ns);
+    return p;
+}
+
+/* free of a large block: 0 pages if addr is not the start of a live one */
+static __device__ uint32_t large_release(gf_heap *H, uint64_t addr, int64_t timeout_ns)
+{
+    const uint64_t off = addr - H->large_base;
+    if (off & ((1ull << GF_PAGE_SHIFT) - 1))
+        return 0;
+    const uint32_t pg = (uint32_t)(off >> GF_PAGE_SHIFT);
+    /* claim the block: of two frees of one pointer only one sees its size */
+    const uint32_t np = atomicExch(&((uint32_t *)H->large_size)[pg], 0u);
+    if (np == 0)
+        return 0;
+    const unsigned long long old =
+        atomicExch((unsigned long long *)&H->large_cache, (unsigned long long)pg | ((unsigned long long)np << 32));
+    if (old && !large_insert(H, (uint32_t)old, (uint32_t)(old >> 32), timeout_ns))
+        set_error(GF_ETIMEDOUT);              /* the lock never came: those pages leak */
+    return np;
+}
+
 } // namespace gfd
 
 /* ====================================================================== malloc / free */
@@ -337,7 +376,7 @@ static __device__ __forceinline__ void *gf_malloc_body(size_t n)
     gf_state *S = gfd::s_st;
     gf_heap *H = &S->heap;
     if (n > GF_HEAP_MAX_SMALL) {
-        void *p = gfd::large_alloc(H, n, S->timeout_ns);
+        void *p = gfd::large_malloc(H, n, S->timeout_ns);
         atomicAdd((unsigned long long *)(p ? &H->n_alloc : &H->n_fail), 1ull);
         if (p) {
             const unsigned long long pb = ((unsigned long long)n + (1ull << GF_PAGE_SHIFT) - 1) &
@@ -415,9 +454,9 @@ static __device__ __forceinline__ void gf_free_body(void *p)
     const uint32_t grp = __match_any_sync(active, key);
     if (!small) {
         if (a >= H->large_base && a < H->large_base + H->large_bytes) {
-            const uint32_t pg = (uint32_t)((a - H->large_base) >> GF_PAGE_SHIFT);
-            const uint64_t bytes = (uint64_t)(*(volatile uint32_t *)&((uint32_t *)H->large_size)[pg]) << GF_PAGE_SHIFT;
-            if (gfd::large_free(H, a, S->timeout_ns)) {
+            const uint32_t np = gfd::large_release(H, a, S->timeout_ns);
+            if (np) {
+                const uint64_t bytes = (uint64_t)np << GF_PAGE_SHIFT;
                 atomicAdd((unsigned long long *)&H->n_free, 1ull);
                 atomicAdd((unsigned long long *)&H->live_bytes, (unsigned long long)(0ull - bytes));
                 return;

@@ -161,6 +161,7 @@ typedef struct gf_heap {
     uint32_t pad;
     uint64_t live_bytes, high_water;
     uint64_t n_alloc, n_free, n_fail, n_bad_free;
+    uint64_t large_cache;      /* the last freed large block {page, npages << 32}, 0 if none */
 } gf_heap;
 
 /* ------------------------------------------------------------------ program state */
