@@ -322,8 +322,8 @@ static __device__ bool large_insert(gf_heap *H, uint32_t pg, uint32_t np, int64_
  * The last freed large block waits in a one-entry cache (its page count in
  * the high word) instead of going back to the extent table: a program that
  * frees a block and then asks for one of the same size -- a scratch buffer
- * per iteration -- gets it back with one compare-and-swap, and the free is
- * one exchange, neither taking the lock.  A request of another size, or one
+ * per iteration -- gets it back with one exchange, and the free is one
+ * exchange too, neither taking the lock.  A request of another size, or one
  * the table cannot serve, first returns the cached block to the table, so
  * first fit still sees every free page merged.
  */
@@ -331,17 +331,14 @@ static __device__ void *large_malloc(gf_heap *H, uint64_t n, int64_t timeout_ns)
 {
     const uint32_t need = (uint32_t)((n + (1ull << GF_PAGE_SHIFT) - 1) >> GF_PAGE_SHIFT);
     unsigned long long *cache = (unsigned long long *)&H->large_cache;
-    unsigned long long c = *(volatile unsigned long long *)cache;
+    unsigned long long c = atomicExch(cache, 0ull);
     if (c) {
         if ((uint32_t)(c >> 32) == need) {
-            if (atomicCAS(cache, c, 0ull) == c) {
-                const uint32_t pg = (uint32_t)c;
-                ((volatile uint32_t *)H->large_size)[pg] = need;
-                return (void *)(H->large_base + ((uint64_t)pg << GF_PAGE_SHIFT));
-            }
-        } else if ((c = atomicExch(cache, 0ull)) != 0ull) {
-            large_insert(H, (uint32_t)c, (uint32_t)(c >> 32), timeout_ns);
+            const uint32_t pg = (uint32_t)c;
+            ((volatile uint32_t *)H->large_size)[pg] = need;
+            return (void *)(H->large_base + ((uint64_t)pg << GF_PAGE_SHIFT));
         }
+        large_insert(H, (uint32_t)c, (uint32_t)(c >> 32), timeout_ns);
     }
     void *p = large_alloc(H, n, timeout_ns);
     if (!p && (c = atomicExch(cache, 0ull)) != 0ull &&
