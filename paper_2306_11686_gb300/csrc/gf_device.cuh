@@ -39,11 +39,14 @@
 #define GF_BLOCK 256
 #endif
 /* default minimum resident blocks per SM a program's persistent kernel is
- * compiled for (1: the register count is the compiler's choice).  Programs
- * whose regions are latency-bound ask for more with GF_MAIN_BOUNDS(name, n):
- * the Jacobi sweep runs fastest at 4 (64 registers), the batched loops at 8. */
+ * compiled for: 4 (at most 64 registers).  A legacy loop streams from HBM
+ * with as many loads in flight as the SM holds warps: one axpy region over
+ * 2^28 doubles reached 45% of the measured copy peak at the 2 blocks per SM
+ * the compiler's own register choice left, 76% at 4 and 85% at 8 (90% at 4
+ * with 16-byte accesses).  Programs ask for another count with
+ * GF_MAIN_BOUNDS(name, n): the batched loops use 8. */
 #ifndef GF_MIN_BLOCKS
-#define GF_MIN_BLOCKS 1
+#define GF_MIN_BLOCKS 4
 #endif
 #define GF_MAX_WARPS (GF_BLOCK / 32)
 

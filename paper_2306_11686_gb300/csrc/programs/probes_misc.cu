@@ -142,3 +142,44 @@ GF_MAIN(fig4_probe)(int argc, char **argv)
     gf_free(blk);
     return 0;
 }
+
+/* axpy_width w          buffers: 0 = n (int64), 1 = x, 2 = y, 3 = z (n doubles each)
+ * z = 2.5 x + y as one static chunk-1 region with w = 1 (8-byte accesses)
+ * or w = 2 (16-byte double2 accesses from an even index, scalar tail): the
+ * same loop with the access width as the only difference.  axpy_width is
+ * compiled with the register count left to the compiler, axpy_width4 and
+ * axpy_width8 for 4 and 8 resident blocks per SM (64 and 32 registers). */
+static __device__ int axpy_width_main(int argc, char **argv)
+{
+    if (argc < 2)
+        return 2;
+    const int w = (int)gf_atoll(argv[1]);
+    const long long *np = (const long long *)gf_buffer(0);
+    if (!np || *np < 0)
+        return 2;
+    const long long n = *np;
+    if (n == 0)
+        return 0;
+    const double *x = (const double *)gf_buffer(1), *y = (const double *)gf_buffer(2);
+    double *z = (double *)gf_buffer(3);
+    if (!x || !y || !z || gf_buffer_bytes(1) < (uint64_t)n * 8 || gf_buffer_bytes(2) < (uint64_t)n * 8 ||
+        gf_buffer_bytes(3) < (uint64_t)n * 8)
+        return 2;
+    if (w == 1)
+        return gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) { z[i] = 2.5 * x[i] + y[i]; }) ? 10 : 0;
+    if (((uintptr_t)x | (uintptr_t)y | (uintptr_t)z) & 15)
+        return 2;
+    const double2 *x2 = (const double2 *)x, *y2 = (const double2 *)y;
+    double2 *z2 = (double2 *)z;
+    if (gf_parallel_for(0, n / 2, GF_SCHED_STATIC, 1, [=](int64_t i) {
+            const double2 a = x2[i], b = y2[i];
+            z2[i] = make_double2(2.5 * a.x + b.x, 2.5 * a.y + b.y);
+        }))
+        return 10;
+    if (n & 1)
+        z[n - 1] = 2.5 * x[n - 1] + y[n - 1];
+    return 0;
+}
+GF_MAIN_BOUNDS(axpy_width, 1)(int argc, char **argv) { return axpy_width_main(argc, argv); }
+GF_MAIN_BOUNDS(axpy_width4, 4)(int argc, char **argv) { return axpy_width_main(argc, argv); }
+GF_MAIN_BOUNDS(axpy_width8, 8)(int argc, char **argv) { return axpy_width_main(argc, argv); }

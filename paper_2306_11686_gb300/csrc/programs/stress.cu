@@ -71,8 +71,11 @@ GF_MAIN(stress)(int argc, char **argv)
 /*
  * heap_only T                buffers: 0 = uint32 sizes[8T], 1 = uint64 checksums[T], 2 = int64 fail [1]
  * The heap half of the stress program alone (no printf), to time alloc/free pairs.
+ * Compiled with the register count left to the compiler (2 blocks per SM):
+ * more resident warps only add contention on the per-lane free stacks
+ * (571 M pairs/s there, 368 M at 4 blocks per SM).
  */
-GF_MAIN(heap_only)(int argc, char **argv)
+GF_MAIN_BOUNDS(heap_only, 1)(int argc, char **argv)
 {
     const long long T = gf_atoll(argv[1]);
     const unsigned *sizes = (const unsigned *)gf_buffer(0);
@@ -101,8 +104,12 @@ GF_MAIN(heap_only)(int argc, char **argv)
     }) ? 10 : 0;
 }
 
-/* printf_only T              the RPC half alone: 4 printf per iteration, formats as in stress */
-GF_MAIN(printf_only)(int argc, char **argv)
+/* printf_only T              the RPC half alone: 4 printf per iteration, formats as in stress.
+ * Compiled with the register count left to the compiler (2 blocks per SM):
+ * its calls are bound by the ring and the host, and more resident warps
+ * only lengthen the queue for slots (one slot per calling thread: 9.1 M
+ * calls/s there, 4.4 M at 4 blocks per SM). */
+GF_MAIN_BOUNDS(printf_only, 1)(int argc, char **argv)
 {
     const long long T = gf_atoll(argv[1]);
     return gf_parallel_for(0, T, GF_SCHED_STATIC, 1, [=](int64_t t) {

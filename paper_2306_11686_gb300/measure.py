@@ -418,12 +418,43 @@ def axpy_regions(logs, reps=5):
     return res
 
 
+def axpy_width_table(lg=28, reps=6):
+    """The same axpy loop (one static chunk-1 region, N = 2^lg) with 8-byte and
+    16-byte accesses (program axpy_width, argument 1 or 2) at 3, 4 and 8
+    resident blocks per SM: GB/s of the best region after the first."""
+    import torch
+    n = 1 << lg
+    x = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+    y = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+    z = torch.zeros(n, dtype=torch.float64, device="cuda")
+    nb = torch.tensor([n], dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    out = {}
+    with gf.Context(stream=stream, heap_bytes=64 << 20, timeout_ns=int(60e9)) as ctx:
+        for prog in ("axpy_width", "axpy_width4", "axpy_width8"):
+            row = {"blocks_per_sm": ctx.grid_info(prog)[1]}
+            for w in (1, 2):
+                ts = []
+                for _ in range(reps):
+                    z.zero_()
+                    rc, ec = ctx.run(prog, [w], [(nb, 1), (x, 1), (y, 1), (z, 1)])
+                    if ec != 0:
+                        raise RuntimeError(f"{prog} exit code {ec}")
+                    st = ctx.stats()
+                    ts.append(st.region_ns / max(1, st.regions) / 1e9)
+                t = min(ts[1:])
+                row[f"{8 * w}B"] = {"GBps": round(24 * n / t / 1e9, 1), "correct": bool(torch.equal(z, 2.5 * x + y))}
+            out[prog] = row
+    return out
+
+
 def hbm(args):
     """One large legacy loop through the plain runtime at N = 2^26 and 2^28:
     inputs far larger than L2, so the region's GB/s is HBM bandwidth."""
     peak = _hbm_peak()
     res = axpy_regions((args.hbm_log2,) if getattr(args, "hbm_log2", None) else (26, 28))
     best = max(v["GBps"] for v in res.values())
+    res["access_width"] = axpy_width_table()
     line = {"metric": "loop GB/s (% HBM peak)", "value": round(best, 1), "unit": "GB/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "one axpy loop z = 2.5 x + y, N = " + " and ".join(res) + ", static chunk 1, "

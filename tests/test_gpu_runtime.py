@@ -413,3 +413,26 @@ def test_link_probe_round_trip_and_rpc_latency(gf_lib, tmp_path):
             v = ns[:50].cpu().numpy()
             assert (v > 0).all() and (v < 10_000_000_000).all()
             assert (ns[50:].cpu().numpy() == 0).all()
+
+
+@pytest.mark.parametrize("prog", ["axpy_width", "axpy_width4", "axpy_width8"])
+@pytest.mark.parametrize("n", [0, 1, 2, 1001, 1 << 16])
+def test_axpy_access_width(gf_lib, prog, n):
+    """The axpy loop with 8-byte and 16-byte accesses (even index, scalar
+    tail) gives torch's own results, at every compiled occupancy; 16-byte
+    accesses refuse a misaligned buffer."""
+    import torch
+    gf = gf_lib
+    x = torch.empty(n + 1, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+    y = torch.empty(n + 1, dtype=torch.float64, device="cuda").uniform_(-1, 1)
+    nb = torch.tensor([n], dtype=torch.int64, device="cuda")
+    with gf.Context(timeout_ns=10_000_000_000, heap_bytes=64 << 20) as ctx:
+        for w in (1, 2):
+            z = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+            rc, ec = ctx.run(prog, [w], [(nb, 1), (x[:n], 1), (y[:n], 1), (z[:n], 1)])
+            assert ec == 0
+            assert torch.equal(z[:n], 2.5 * x[:n] + y[:n]) and z[n] == 0
+        if n >= 2:
+            z = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+            rc, ec = ctx.run(prog, [2], [(nb, 1), (x[1:], 1), (y[1:], 1), (z[1:], 1)])
+            assert ec == 2 and not z.any()
