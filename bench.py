@@ -250,7 +250,7 @@ def main():
                          "aggregation, one axpy loop at 2^28 against HBM, the measured FP64 add peak)")
     ap.add_argument("--no-write", action="store_true",
                     help="the program skips its final fwrite (profiling runs that isolate the sweeps)")
-    ap.add_argument("--workload", default="jacobi", choices=["jacobi", "stress", "batch", "learned", "serve", "e1", "link", "hbm", "split"],
+    ap.add_argument("--workload", default="jacobi", choices=["jacobi", "stress", "batch", "learned", "serve", "spmv", "e1", "link", "hbm", "split"],
                     help="jacobi = the benchmark; the others measure the RPC/heap stress, 256-loop batching, "
                          "learned launch shapes, serving, host-link peaks, single large loops and the "
                          "persistent grid against the paper's kernel split")

@@ -249,6 +249,27 @@ def _spmv_alone(serve, n, P, tmp, fp64_peak=None):
     return out
 
 
+def spmv(args):
+    """The served SpMV alone: one request-free program (10 passes of a 1 M-row
+    CSR SpMV, 16 nonzeros per row) after a warm-up, against the HBM and FP64
+    peaks."""
+    import ctypes
+    from . import serve
+    tmp = tempfile.mkdtemp(prefix="gfspmv", dir=_out_dir(args))
+    ms, adds = ctypes.c_float(), ctypes.c_double()
+    gf.gf_fp64_add_rate(0, 512, None, ctypes.byref(ms), ctypes.byref(adds))
+    peak = adds.value / (ms.value / 1e3)
+    one = _spmv_alone(serve, 1 << 20, 1, tmp, peak)
+    line = {"metric": "loop GB/s (% HBM peak)", "value": round(one["GBps"], 1), "unit": "GB/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "CSR SpMV 1M rows x 16 nnz, 10 passes, one program, no requests"},
+            "roofline": {"bound": "fp64", "achieved": round(one["fp64_Gops"], 1), "peak": round(peak / 1e9, 1),
+                         "unit": "G FP64 op/s", "frac": round(one["fp64_frac"], 4)},
+            "detail": one}
+    print(json.dumps(line))
+    shutil.rmtree(tmp, ignore_errors=True)
+
+
 def serve_run(args):
     import ctypes
     from . import serve
@@ -524,5 +545,5 @@ def split(args):
 
 
 def run(args):
-    {"stress": stress, "batch": batch, "learned": learned, "serve": serve_run, "e1": e1,
+    {"stress": stress, "batch": batch, "learned": learned, "serve": serve_run, "spmv": spmv, "e1": e1,
      "link": link, "hbm": hbm, "split": split}[args.workload](args)
