@@ -73,6 +73,18 @@ __shared__ unsigned long long s_pend_key;  /* ... and the format it shipped (0: 
 __shared__ unsigned long long s_done_t1;   /* last deferred call collected with its value */
 __shared__ long long s_done_val;
 __shared__ unsigned long long s_known_key; /* a format the host is known to have         */
+/* printf records of the initial thread waiting to share one ring slot (the
+ * stdio buffer of the serial part): the records, their count and bytes, the
+ * format they share and whether it ships with them, and the sequence numbers
+ * that name each buffered call */
+#define GF_PBUF_WORDS 128
+__shared__ uint64_t s_pb[GF_PBUF_WORDS];
+__shared__ uint32_t s_pb_n, s_pb_bytes, s_pb_fbytes, s_pend_n;
+__shared__ unsigned long long s_pb_key;    /* format (device address) of the buffered records */
+__shared__ const char *s_pb_fmt;
+__shared__ unsigned long long s_pb_seq;    /* sequence number of the next buffered call        */
+__shared__ unsigned long long s_pend_seq0; /* first sequence number in the pending slot, 0: one
+                                              unbuffered call                                 */
 
 /* how long the initial thread polls a region's end without sleeping, and
  * the workers poll for the next region with short sleeps */
@@ -145,6 +157,14 @@ __device__ __forceinline__ void block_setup(gf_state *S, uint32_t kr)
     s_done_t1 = 0;
     s_done_val = -1;
     s_known_key = 0;
+    s_pb_n = 0;
+    s_pb_bytes = 0;
+    s_pb_fbytes = 0;
+    s_pend_n = 0;
+    s_pb_key = 0;
+    s_pb_fmt = nullptr;
+    s_pb_seq = 1;
+    s_pend_seq0 = 0;
 }
 __device__ __forceinline__ bool is_initial_thread() { return blockIdx.x == 0 && threadIdx.x == 0 && !s_kr; }
 
@@ -812,6 +832,7 @@ __global__ void __launch_bounds__(GF_BLOCK, MINB) program_kernel(gf_state *S, in
         if (threadIdx.x == 0) {
             S->t_main_start = now_ns();
             int rc = MAIN(argc, argv);
+            pb_flush(S);                      /* printf records main left buffered */
             rpc_collect_deferred(S, false);   /* a printf main did not wait for */
             S->exit_code = rc;
             S->t_main_end = now_ns();

@@ -222,13 +222,21 @@ __device__ __forceinline__ void st_relaxed_sys64(uint64_t *p, uint64_t v)
  * RPC the result is not read, and the give-back needs no ordering beyond
  * the acquire that saw the answer.  Initial thread only.
  */
-static __device__ __noinline__ uint64_t rpc_collect_deferred(gf_state *S, bool want_ret)
+/* names a buffered call in a gf_call_result (the rest is its sequence number) */
+#define GF_CALL_BUFFERED (1ull << 63)
+
+static __device__ __noinline__ uint64_t rpc_collect_deferred(gf_state *S, bool want_ret, uint32_t rank = 0)
 {
     const unsigned long long t1 = s_pend_t1;
     if (!t1)
         return 0;
     const unsigned long long t = t1 - 1;
+    const unsigned long long seq0 = s_pend_seq0;
+    const uint32_t n = seq0 ? s_pend_n : 1u;
     s_pend_t1 = 0;
+    /* the name the program holds for the record asked for: the ticket of a
+     * lone call, the sequence number of a buffered one */
+    const unsigned long long name = seq0 ? (GF_CALL_BUFFERED | (seq0 + rank)) : t1;
     uint8_t *slot = (uint8_t *)(S->ring_slots + (t % S->nslots) * (uint64_t)S->slot_bytes);
     gf_slot_hdr *h = (gf_slot_hdr *)slot;
     const uint64_t t0 = now_ns();
@@ -236,7 +244,7 @@ static __device__ __noinline__ uint64_t rpc_collect_deferred(gf_state *S, bool w
     while (ld_acq_sys64(&h->seq) != t + 2)
         if (!bo.wait()) {
             set_error(GF_ETIMEDOUT);
-            s_done_t1 = t1;
+            s_done_t1 = name;
             s_done_val = -1;
             return now_ns() - t0;
         }
@@ -244,21 +252,115 @@ static __device__ __noinline__ uint64_t rpc_collect_deferred(gf_state *S, bool w
     const uint32_t op = GF_OP_PRINTF;            /* the only deferred calls */
     atomicAdd((unsigned long long *)&S->st_wait_ns, (unsigned long long)waited);
     atomicAdd((unsigned long long *)&S->st_wait_op_ns[op], (unsigned long long)waited);
-    atomicAdd((unsigned long long *)&S->st_calls[op], 1ull);
+    atomicAdd((unsigned long long *)&S->st_calls[op], (unsigned long long)n);
     atomicAdd((unsigned long long *)&S->st_slots[op], 1ull);
     if (s_pend_key) {
         fmt_insert(S, s_pend_key);
         s_known_key = s_pend_key;
     }
-    if (want_ret) {
-        s_done_val = (long long)ld_vol64((const uint64_t *)(slot + GF_SLOT_RET_OFF));
-        s_done_t1 = t1;
+    if (want_ret && rank < n) {
+        s_done_val = (long long)ld_vol64((const uint64_t *)(slot + GF_SLOT_RET_OFF) + rank);
+        s_done_t1 = name;
         st_rel_sys64(&h->seq, t + S->nslots);
     } else {
         s_done_t1 = 0;
         st_relaxed_sys64(&h->seq, t + S->nslots);
     }
     return waited;
+}
+
+/*
+ * The initial thread's printf records wait in its block's shared memory and
+ * go to the host together, up to 32 in one ring slot (the role of stdio's
+ * buffer in the serial program): a call costs the packing of its record,
+ * and one slot claim, credit check and publication serve the whole batch.
+ * The batch is sent when it is full, before a record with another format,
+ * before any other RPC of the initial thread (so its calls still reach the
+ * host in program order), when a buffered call's result is read, and when
+ * main returns.  Records of other threads are not ordered against it, as
+ * for any two threads' calls.
+ */
+static __device__ __noinline__ void pb_flush(gf_state *S)
+{
+    const uint32_t n = s_pb_n;
+    if (!n)
+        return;
+    s_pb_n = 0;
+    const uint32_t bytes = s_pb_bytes, fbytes = s_pb_fbytes;
+    s_pb_bytes = 0;
+    if (s_pend_t1)                                  /* the previous slot is answered first */
+        rpc_collect_deferred(S, false);
+    if (*(volatile int32_t *)&S->error)
+        return;                                     /* the program failed: the records are dropped */
+    const unsigned long long t = atomicAdd(&S->rpc_ticket, 1ull);
+    uint8_t *slot = (uint8_t *)(S->ring_slots + (t % S->nslots) * (uint64_t)S->slot_bytes);
+    gf_slot_hdr *h = (gf_slot_hdr *)slot;
+    const uint64_t t_issue = now_ns();
+    backoff bo(S->timeout_ns);
+    while (ld_acq_sys64(&h->seq) != t)
+        if (!bo.wait()) {
+            set_error(GF_ERING);
+            return;
+        }
+    uint8_t *payload = slot + GF_SLOT_PAYLOAD_OFF;
+    const uint32_t fmt_len = fbytes ? gf_strlen(s_pb_fmt) + 1u : 0u;
+    if (fbytes)
+        copy_out((uint64_t *)payload, s_pb_fmt, fmt_len);
+    uint64_t *dst = (uint64_t *)(payload + fbytes);
+    for (uint32_t w = 0; w < bytes / 8; w++)
+        dst[w] = s_pb[w];
+    h->opcode = GF_OP_PRINTF;
+    h->nlanes = n;
+    h->flags = fbytes ? GF_SF_FMT_INLINE : 0u;
+    h->fmt_len = fmt_len;
+    h->fmt_key = s_pb_key;
+    h->prog = S->prog_id;
+    h->t_issue = t_issue;
+    h->payload_bytes = 0;
+    h->t_publish = now_ns();
+    st_rel_sys64(&h->seq, t + 1);                   /* orders this thread's record writes before it */
+    s_pend_t1 = t + 1;
+    s_pend_key = fbytes ? s_pb_key : 0ull;
+    s_pend_seq0 = s_pb_seq - n;
+    s_pend_n = n;
+}
+
+/* buffer one printf of the initial thread; false: it takes the unbuffered path */
+static __device__ __noinline__ bool pb_printf(const char *fmt, const argpack &a, unsigned long long *name)
+{
+    gf_state *S = s_st;
+    const uint64_t t_enter = now_ns();
+    if (!fmt || *(volatile int32_t *)&S->error)
+        return false;
+    const uint64_t key = (uint64_t)fmt;
+    const uint32_t my = a.bytes(), slot_cap = S->slot_bytes - GF_SLOT_PAYLOAD_OFF;
+    if (s_pb_n && key != s_pb_key)
+        pb_flush(S);
+    for (int pass = 0; pass < 2; pass++) {
+        if (!s_pb_n) {                              /* a new batch: does its format ship with it? */
+            const bool ship = key != s_known_key && !fmt_known(S, key);
+            if (!ship)
+                s_known_key = key;
+            s_pb_fbytes = ship ? (gf_strlen(fmt) + 1u + 7u) & ~7u : 0u;
+            s_pb_key = key;
+            s_pb_fmt = fmt;
+        }
+        const uint32_t room = slot_cap > s_pb_fbytes ? slot_cap - s_pb_fbytes : 0u;
+        const uint32_t cap = room < 8u * GF_PBUF_WORDS ? room : 8u * GF_PBUF_WORDS;
+        if (s_pb_bytes + my <= cap)
+            break;
+        if (!s_pb_n)
+            return false;                           /* larger than the buffer: sent on its own */
+        pb_flush(S);
+    }
+    write_rec((uint8_t *)s_pb + s_pb_bytes, a, s_pb_n, 0xffffffffu);
+    s_pb_bytes += my;
+    s_pb_n++;
+    *name = GF_CALL_BUFFERED | s_pb_seq++;
+    if (s_pb_n == 32)
+        pb_flush(S);
+    atomicAdd((unsigned long long *)&S->st_client_ns, (unsigned long long)(now_ns() - t_enter));
+    return true;
 }
 
 /*
@@ -278,7 +380,9 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
     const bool initial = is_initial_thread();
     const uint64_t t_enter = initial ? now_ns() : 0;
     uint64_t t_waited = 0;                          /* this call's waits for the host */
-    if (initial && s_pend_t1)                       /* keep the initial thread's calls in order */
+    if (initial && s_pb_n)                          /* keep the initial thread's calls in order */
+        pb_flush(S);
+    if (initial && s_pend_t1)
         t_waited += rpc_collect_deferred(S, false);
     {
         /* fail fast after the first error; one reading for the whole group */
@@ -403,6 +507,7 @@ static __device__ __noinline__ int64_t rpc_issue(uint32_t op, const char *fmt, c
             st_rel_sys64(&h->seq, t + 1);
             s_pend_t1 = t + 1;
             s_pend_key = ship ? key : 0;
+            s_pend_seq0 = 0;
             *defer_t1 = t + 1;
             ret = 0;
             continue;
@@ -476,21 +581,31 @@ template <class... A> __device__ inline int64_t rpc(uint32_t op, const char *fmt
     return rpc_issue(op, fmt, a, status);
 }
 
-/* the result of a deferred call, by its ticket + 1 (initial thread only) */
+/* the result of a deferred call (initial thread only), by its name: the
+ * ticket + 1 of a lone call, or GF_CALL_BUFFERED | the sequence number of a
+ * buffered one (sent now if it is still in the buffer) */
 static __device__ __noinline__ int64_t deferred_value(unsigned long long t1)
 {
     gf_state *S = s_st;
-    if (s_pend_t1 == t1)
+    if (t1 & GF_CALL_BUFFERED) {
+        const unsigned long long seq = t1 & ~GF_CALL_BUFFERED;
+        if (s_pb_n && seq >= s_pb_seq - s_pb_n)
+            pb_flush(S);
+        if (s_pend_t1 && s_pend_seq0 && seq >= s_pend_seq0 && seq < s_pend_seq0 + s_pend_n)
+            rpc_collect_deferred(S, true, (uint32_t)(seq - s_pend_seq0));
+    } else if (s_pend_t1 == t1 && !s_pend_seq0) {
         rpc_collect_deferred(S, true);
+    }
     return s_done_t1 == t1 ? (int64_t)s_done_val : -1;
 }
 } // namespace gfd
 
 /* Result of a printf-family call.  Converting it to int gives the call's
- * return value (waiting for the host if the call was deferred); a program
- * that ignores it never waits for the call.  Use it in the statement that
- * made the call: a deferred result converted after a later RPC of the
- * initial thread reads -1. */
+ * return value (sending the initial thread's buffered records and waiting
+ * for the host if the call was buffered or deferred); a program that
+ * ignores it never waits for the call.  Use it in the statement that made
+ * the call: a deferred result converted after a later RPC of the initial
+ * thread, or after its batch went to the host with later calls, reads -1. */
 struct gf_call_result {
     int64_t v;
     unsigned long long t1;     /* ticket + 1 of a deferred call; 0: v is the result */
@@ -504,6 +619,8 @@ template <class... A> __device__ inline gf_call_result rpc_deferrable(uint32_t o
     pack_all(a, args...);
     if (is_initial_thread()) {
         unsigned long long t1 = 0;
+        if (op == GF_OP_PRINTF && pb_printf(fmt, a, &t1))
+            return gf_call_result{0, t1};
         const int64_t r = rpc_issue(op, fmt, a, nullptr, &t1);
         return gf_call_result{t1 ? 0 : r, t1};
     }
@@ -524,6 +641,8 @@ static __device__ __noinline__ int rpc_post1(uint32_t op, const argpack &a, unsi
     gf_state *S = s_st;
     if (a.bytes() > S->slot_bytes - GF_SLOT_PAYLOAD_OFF)
         return GF_EINVAL;
+    if (s_pb_n)
+        pb_flush(S);
     if (s_pend_t1)
         rpc_collect_deferred(S, false);
     if (*(volatile int32_t *)&S->error)

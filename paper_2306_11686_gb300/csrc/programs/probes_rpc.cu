@@ -178,3 +178,37 @@ GF_MAIN(rpc_timeout)(int argc, char **argv)
     gfd::rpc(GF_OP_CLOCK, nullptr, &st);
     return st == GF_ETIMEDOUT ? 1 : (st == GF_OK ? 0 : 2);
 }
+
+/*
+ * main_printf_batch          buffers: 0 = int64 results[8]
+ * The initial thread's buffered printf: 100 lines of one format (three full
+ * batches and a partial one), a line of another format with a string, a
+ * result read in its own statement, a non-printf call (clock) in between, a
+ * record too large for the buffer, 40 lines of a third format, a result
+ * read only after a later call (-1 by contract), then main returns with
+ * records still buffered.  Every line must appear once, in program order.
+ */
+GF_MAIN(main_printf_batch)(int argc, char **argv)
+{
+    long long *res = (long long *)gf_buffer(0);
+    if (!res)
+        return 2;
+    for (int k = 0; k < 100; k++)
+        gf_printf("a %d\n", k);
+    gf_printf("b %s %d\n", "str", -1);
+    res[0] = (int)gf_printf("c %d\n", 7);               /* read at once: 4 */
+    res[1] = gf_clock() >= 0 ? 1 : 0;
+    char big[1400];
+    for (int k = 0; k < 1399; k++)
+        big[k] = (char)('a' + k % 26);
+    big[1399] = 0;
+    res[2] = (int)gf_printf("big %s\n", big);            /* larger than the buffer: 1404 */
+    gf_call_result late = gf_printf("d %d %.17g\n", 0, 0.5);
+    for (int k = 1; k < 40; k++)
+        gf_printf("d %d %.17g\n", k, k * 0.25);
+    res[3] = gf_clock() >= 0 ? 1 : 0;
+    res[4] = (int)late;                                   /* its batch already went: -1 */
+    gf_printf("e %d\n", 1);
+    gf_printf("e %d\n", 2);                              /* left buffered when main returns */
+    return 0;
+}

@@ -436,3 +436,26 @@ def test_axpy_access_width(gf_lib, prog, n):
             z = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
             rc, ec = ctx.run(prog, [2], [(nb, 1), (x[1:], 1), (y[1:], 1), (z[1:], 1)])
             assert ec == 2 and not z.any()
+
+
+def test_main_printf_buffered(gf_lib, tmp_path):
+    """The initial thread's printf records share ring slots: every line once
+    and in program order across full and partial batches, format changes,
+    a string argument, a record larger than the buffer, other calls in
+    between and records still buffered when main returns; a result read in
+    its own statement is the character count; fewer slots than calls."""
+    import torch
+    gf = gf_lib
+    res = torch.zeros(8, dtype=torch.int64, device="cuda")
+    with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20) as c:
+        rc, ec = c.run("main_printf_batch", [], [(res, 1)])
+        st = c.stats()
+    assert ec == 0
+    big = "".join(chr(ord("a") + k % 26) for k in range(1399))
+    want = [f"a {k}" for k in range(100)] + ["b str -1", "c 7", "big " + big]
+    want += ["d %d %.17g" % (k, 0.5 if k == 0 else k * 0.25) for k in range(40)] + ["e 1", "e 2"]
+    assert open(tmp_path / "out.txt").read().splitlines() == want
+    r = res.cpu().tolist()
+    assert r[0] == 4 and r[1] == 1 and r[2] == len("big ") + 1399 + 1 and r[3] == 1 and r[4] == -1
+    assert st.rpc_calls[gf.OP_PRINTF] == len(want)
+    assert st.rpc_slots[gf.OP_PRINTF] <= 14                # 145 calls in at most 14 slots
