@@ -11,6 +11,7 @@
 #include <time.h>
 #include <unistd.h>
 
+#include <algorithm>
 #include <condition_variable>
 #include <thread>
 #include <chrono>
@@ -36,6 +37,7 @@ void Segment::reset(uint32_t nthreads)
     for (uint32_t t = 0; t < nthreads; t++)
         cursor[t] = t;                  /* thread t serves slots t, t + nthreads, ... */
     passes.assign(nthreads, 0);
+    pending.assign(nthreads, {});
     std::lock_guard<std::mutex> g(fmt_mu);
     fmt_cache.clear();
     fmt_local.assign(nthreads, {});
@@ -886,22 +888,17 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
         tid < seg.fmt_local.size() ? &seg.fmt_local[tid] : nullptr;
     /* Claims arrive in ticket order, so the next request is usually in the
      * slot after the last one served: start there and stop after a run of
-     * quiet slots; every 64th pass scans all of this thread's slots to pick
-     * up requests published late behind the cursor. */
-    const bool full = (++seg.passes[tid] & 63u) == 0;
-    uint32_t s = seg.cursor[tid];
-    for (uint32_t k = 0; k < N; k += nthr, s = (s + nthr) % N) {
-        if (!full && gap >= 64)
-            break;
+     * quiet slots.  A slot passed while its claimant was still writing it
+     * (its ticket below one served later) goes on this thread's pending
+     * list; every 64th pass also scans all of this thread's slots. */
+    /* serve slot s if it holds its expected ticket's published request */
+    auto try_slot = [&](uint32_t s) -> bool {
         uint8_t *slot = seg.slots + (uint64_t)s * seg.slot_bytes;
         gf_slot_hdr *h = (gf_slot_hdr *)slot;
         const uint64_t t = seg.expect[s];
         const uint64_t q = acquire_load(&h->seq);
-        if (q != t + 1) {
-            gap++;
-            continue;
-        }
-        gap = 0;
+        if (q != t + 1)
+            return false;
         const uint64_t t0 = now_ns();
         const uint32_t op = h->opcode, nl = h->nlanes;
         uint8_t *pay = slot + GF_SLOT_PAYLOAD_OFF;
@@ -1002,7 +999,6 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
         n_ring += (uint64_t)(pay - slot) + 8ull * nl;
         n_op[op < GF_NSTAT ? op : 0] += nl;
         seg.expect[s] = t + N;
-        seg.cursor[tid] = (s + nthr) % N;
         if (hold) {
             held[nheld] = &h->seq;
             held_t[nheld] = t + 2;
@@ -1011,6 +1007,44 @@ int Server::poll_active(Segment &seg, uint32_t tid, uint32_t nthr)
         } else {
             release_store(&h->seq, t + 2);
         }
+        return true;
+    };
+    /* slots whose ticket was claimed before a later one was served, but
+     * which were still unpublished when the scan passed them: looked at
+     * first, every pass, until served (a slow claimant costs one load per
+     * pass instead of waiting for the full scan) */
+    std::vector<uint32_t> &pend = seg.pending[tid];
+    for (size_t i = 0; i < pend.size();) {
+        if (try_slot(pend[i])) {
+            pend[i] = pend.back();
+            pend.pop_back();
+        } else {
+            i++;
+        }
+    }
+    const bool full = (++seg.passes[tid] & 63u) == 0;
+    uint32_t s = seg.cursor[tid];
+    uint32_t quiet[64];
+    uint32_t nq = 0;
+    for (uint32_t k = 0; k < N; k += nthr, s = (s + nthr) % N) {
+        if (!full && gap >= 64)
+            break;
+        if (!try_slot(s)) {
+            gap++;
+            if (nq < 64)
+                quiet[nq++] = s;
+            continue;
+        }
+        gap = 0;
+        seg.cursor[tid] = (s + nthr) % N;
+        /* the quiet slots just passed hold lower tickets than this one: their
+         * claimants exist (tickets are handed out in order) */
+        const uint64_t ts = seg.expect[s] - N;
+        for (uint32_t j = 0; j < nq; j++)
+            if (seg.expect[quiet[j]] < ts && pend.size() < 256 &&
+                std::find(pend.begin(), pend.end(), quiet[j]) == pend.end())
+                pend.push_back(quiet[j]);
+        nq = 0;
     }
     flush();
     if (served) {

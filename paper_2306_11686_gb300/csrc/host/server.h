@@ -115,6 +115,8 @@ struct Segment {
     std::vector<uint64_t> expect;   /* next ticket each slot will carry               */
     std::vector<uint32_t> cursor;   /* per server thread: slot to start the next scan */
     std::vector<uint32_t> passes;   /* per server thread: scans so far                */
+    std::vector<std::vector<uint32_t>> pending;   /* per server thread: claimed slots the scan
+                                                     passed before their publication         */
     std::unordered_map<uint64_t, FmtEntry> fmt_cache;      /* fmt_key -> format (never overwritten) */
     std::mutex fmt_mu;
     /* per server thread: fmt_key -> the entry in fmt_cache, so a thread
