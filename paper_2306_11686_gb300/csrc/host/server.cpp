@@ -277,16 +277,20 @@ class AsyncFile {
         if (err_)
             return -1;
         q_.insert(q_.end(), p, p + n);
+        queued_ += n;
         if (q_.size() >= CHUNK && !busy_)  /* wake the writer for whole chunks only */
             cv_.notify_one();
         return (ssize_t)n;
     }
+    /* wait until the bytes queued before this call are in the file (bytes
+     * other threads queue meanwhile are not waited for) */
     int drain()
     {
         std::unique_lock<std::mutex> lk(mu_);
+        const uint64_t target = queued_;
         drain_++;
         cv_.notify_one();
-        idle_.wait(lk, [&] { return (q_.empty() && !busy_) || err_; });
+        idle_.wait(lk, [&] { return written_ >= target || err_; });
         drain_--;
         return err_ ? -1 : 0;
     }
@@ -323,10 +327,12 @@ class AsyncFile {
                 }
                 off += (size_t)w;
             }
+            const uint64_t wrote = buf.size();
             buf.clear();
             {
                 std::lock_guard<std::mutex> g(mu_);
                 busy_ = false;
+                written_ += wrote;
                 if (bad)
                     err_ = true;
             }
@@ -336,6 +342,7 @@ class AsyncFile {
     }
     static const size_t LIMIT = 64u << 20, CHUNK = 1u << 20;
     int drain_ = 0;
+    uint64_t queued_ = 0, written_ = 0;   /* bytes queued and written since the open */
     int fd_;
     std::mutex mu_;
     std::condition_variable cv_, idle_, space_;

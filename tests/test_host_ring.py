@@ -32,7 +32,9 @@ def test_ring_scenario(ring_bin, tmp_path, scenario):
 def test_async_output_file(tmp_path):
     """The stdout file written by its own thread: lines from four threads
     (some of 65 KB, in several writes) are whole and in per-thread order
-    after every drain and after close."""
+    after every drain and after close; a drain returns promptly while
+    another thread keeps printing (it waits only for what was queued
+    before it)."""
     exe = str(tmp_path / "async_check")
     subprocess.run(["g++", "-std=c++17", "-O2", "-pthread", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
                     os.path.join(ROOT, "tests", "host", "async_file_check.cpp"),
