@@ -68,6 +68,7 @@ __shared__ uint64_t s_xfer[GF_MAX_WARPS][32]; /* per-warp lane hand-off (heap, r
 /* the initial thread's own bookkeeping, kept in its block's shared memory so
  * that its serial part pays no global-memory round trip for it: */
 __shared__ uint32_t s_done_target;         /* blocks done when the current region ends   */
+__shared__ uint32_t s_main_epoch;          /* the last epoch the initial thread published */
 __shared__ unsigned long long s_pend_t1;   /* deferred call: ticket + 1, 0 = none        */
 __shared__ unsigned long long s_pend_key;  /* ... and the format it shipped (0: none)    */
 __shared__ unsigned long long s_done_t1;   /* last deferred call collected with its value */
@@ -152,6 +153,7 @@ __device__ __forceinline__ void block_setup(gf_state *S, uint32_t kr)
     s_st = S;
     s_kr = kr;
     s_done_target = 0;
+    s_main_epoch = 0;                         /* the state's epoch starts at 0 each launch */
     s_pend_t1 = 0;
     s_pend_key = 0;
     s_done_t1 = 0;
@@ -523,8 +525,9 @@ static __device__ __noinline__ int run_region(gf_state *S)
     S->dyn_next = 0;
     S->red_ticket = 0;
     const uint64_t t0 = now_ns();
-    /* the release orders the descriptor stores above before the epoch */
-    st_rel_gpu(&S->epoch, S->epoch + 1);
+    /* the release orders the descriptor stores above before the epoch; the
+     * initial thread is the epoch's only writer, so it counts it itself */
+    st_rel_gpu(&S->epoch, ++s_main_epoch);
     backoff bo(S->timeout_ns);
     while ((int32_t)(ld_acq_gpu(&S->done_blocks) - target) < 0) {
         if (now_ns() - t0 < GF_REGION_SPIN_NS)   /* most regions end within microseconds: no sleep yet */
@@ -839,7 +842,7 @@ __global__ void __launch_bounds__(GF_BLOCK, MINB) program_kernel(gf_state *S, in
             S->main_done = 1;
             S->exit_flag = 1;
             __threadfence();
-            st_rel_gpu(&S->epoch, S->epoch + 1);
+            st_rel_gpu(&S->epoch, ++s_main_epoch);
         }
         return;
     }

@@ -164,6 +164,19 @@ def _mix(z):
     return z ^ (z >> 31)
 
 
+def test_splitmix64_finaliser_against_published_outputs():
+    """The mixer the stress pin below recomputes is SplitMix64's output
+    function (G. Steele, D. Lea, C. Flood, "Fast splittable pseudorandom
+    number generators", OOPSLA 2014; the constants of S. Vigna's reference
+    splitmix64.c): applied to k times the golden gamma it must give the
+    generator's first outputs from seed 0, as published with that code.
+    This ties the pin's tags and printf values to the published generator
+    rather than to the oracle's own copy of it."""
+    gamma = 0x9E3779B97F4A7C15
+    published = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    assert [_mix((k * gamma) & MASK) for k in (1, 2, 3)] == published
+
+
 def test_stress_oracle_against_memory_model(oracle_bin, tmp_path):
     """Checksums from a word-addressed model of the three tag stores and reads
     (a block of w words; w == 2 makes the middle and last word coincide)."""
