@@ -382,10 +382,13 @@ extern "C" GF_API int gf_finalize(gf_ctx *c)
         t.join();
     c->server.close_all();
     if (c->own_out && c->out) {
+        c->server.set_stdout(nullptr);      /* the server keeps no pointer to the closed stream */
         if (c->aout)
             gfh::async_close(c->aout);
         else
             fclose(c->out);
+        c->out = nullptr;
+        c->aout = nullptr;
     }
     for (Instance *in : c->inst) {
         inst_free(in);

@@ -74,6 +74,7 @@ int main(int argc, char **argv)
         all.insert(all.end(), args.begin(), args.end());
         const std::vector<uint8_t> rec = record(all);
         const int64_t n = srv.call(GF_OP_PRINTF, fmt, rec.data());
+        srv.set_stdout(nullptr);          /* f is closed below, before the server goes */
         fflush(f);
         rewind(f);
         std::string got;

@@ -198,6 +198,7 @@ struct ServerRun {
         for (auto &t : th)
             t.join();
         srv.close_all();
+        srv.set_stdout(nullptr);   /* the caller closes its stream next: the server keeps no pointer to it */
     }
 };
 
