@@ -753,11 +753,59 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
         Stream *st = stream_of(r.word(2), hold);
         if (!st || size == 0)
             return 0;
-        std::lock_guard<std::mutex> g(st->mu);   /* the whole transfer, DMA included */
+        const uint64_t bytes = size * nmemb;
+        if (op == GF_OP_FWRITE && r.tag(3) == GF_T_DMA) {
+            /* device memory to the stream: the first chunk's copy runs
+             * before the stream's lock is taken (other server threads may
+             * write the same file meanwhile); from the first byte written
+             * the lock is held to the end, so the fwrite stays whole */
+            if (!d2h_)
+                return 0;
+            std::unique_lock<std::mutex> lk(st->mu, std::defer_lock);
+            bool open = true;
+            const uint64_t done = d2h_(
+                r.word(3), bytes,
+                [&](const void *c, uint64_t n, uint64_t) {
+                    if (!lk.owns_lock()) {
+                        lk.lock();
+                        if (st->closed) {
+                            open = false;
+                            return false;
+                        }
+                        bulk_settle(st);
+                    }
+                    return fwrite(c, 1, n, st->f) == n;
+                },
+                false);
+            stats.dma_bytes += done;
+            return open ? (int64_t)(done / size) : 0;
+        }
+        if (op == GF_OP_FREAD && r.tag(3) == GF_T_DMA) {
+            /* the stream to device memory: the lock is taken at the first
+             * read, inside the DMA lane's own lock, the same order as fwrite
+             * takes them (a lane is shared by server threads tid, tid + 8, ...) */
+            if (!h2d_)
+                return 0;
+            std::unique_lock<std::mutex> lk(st->mu, std::defer_lock);
+            bool open = true;
+            const uint64_t done = h2d_(r.word(3), bytes, [&](void *c, uint64_t want) -> uint64_t {
+                if (!lk.owns_lock()) {
+                    lk.lock();
+                    if (st->closed) {
+                        open = false;
+                        return 0;
+                    }
+                    bulk_settle(st);
+                }
+                return (uint64_t)fread(c, 1, want, st->f);
+            });
+            stats.dma_bytes += done;
+            return open ? (int64_t)(done / size) : 0;
+        }
+        std::lock_guard<std::mutex> g(st->mu);   /* the whole transfer */
         if (st->closed)
             return 0;
         FILE *f = st->f;
-        const uint64_t bytes = size * nmemb;
         if (r.tag(3) == GF_T_ARENA) {
             /* staged in the bulk arena by the device grid (fwrite) or to be
              * copied out of it by the grid (fread) */
@@ -781,22 +829,7 @@ int64_t Server::call(uint32_t op, const char *fmt, const uint8_t *rec, Segment *
                 return 0;
             return op == GF_OP_FWRITE ? (int64_t)fwrite(b, size, nmemb, f) : (int64_t)fread(b, size, nmemb, f);
         }
-        const uint64_t dev = r.word(3);
-        uint64_t done = 0;
-        if (op == GF_OP_FWRITE) {
-            if (!d2h_)
-                return 0;
-            /* chunks arrive in order; each goes to the stream as it lands
-             * while the next one is copied */
-            done = d2h_(dev, bytes, [&](const void *c, uint64_t n, uint64_t) { return fwrite(c, 1, n, f) == n; },
-                        false);
-        } else {
-            if (!h2d_)
-                return 0;
-            done = h2d_(dev, bytes, [&](void *c, uint64_t want) { return (uint64_t)fread(c, 1, want, f); });
-        }
-        stats.dma_bytes += done;
-        return (int64_t)(done / size);
+        return 0;                                /* an argument tag this call does not take */
     }
     case GF_OP_CLOCK:
         return (int64_t)clock();
