@@ -395,8 +395,7 @@ GF_API int gf_grid_info(gf_ctx *ctx, gf_program prog, uint32_t *sms, uint32_t *b
  * the last call's contents; the ticket that must start at zero is cleared
  * before each launch.  Calls that overlap on the GPU race on the array: do
  * not run two at once.  The first call on each device looks the array's
- * address up (cudaGetSymbolAddress, with that device current) and caches it;
- * make that first call before any stream capture starts.
+ * address up (cudaGetSymbolAddress, with that device current) and caches it.
  * Errors: GF_EINVAL (bad op, n < 0, NULL pointers, too many blocks),
  * GF_ECUDA (lookup, ticket clear or launch failed).  A CUDA error left
  * pending by the caller's earlier work is not read or cleared. */

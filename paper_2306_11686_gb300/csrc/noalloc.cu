@@ -30,8 +30,7 @@
  *    host threads on the same device) race on the array and give wrong
  *    results: serialise them;
  *  - the first call on a device looks up the array's device address with
- *    cudaGetSymbolAddress (with that device current) and caches it; make that
- *    first call before any stream capture begins.
+ *    cudaGetSymbolAddress (with that device current) and caches it.
  */
 #include <cuda_runtime.h>
 #include <functional>
