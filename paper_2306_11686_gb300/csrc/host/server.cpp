@@ -139,9 +139,10 @@ class CopyPool {
  * anything that is not a plain regular file, and small writes, use fwrite.
  *
  * A write the device sends in chunks (the halves of its bulk arena) says in
- * `rest` how many bytes remain including this chunk: the file is sized and
- * the whole range mapped once, at the first chunk, and released after the
- * last one, so the chunks cost no mapping, sizing or unmapping of their own.
+ * `rest` how many bytes remain including this chunk: when its chunks are
+ * large, the file is sized and the whole range mapped once, at the first
+ * chunk, and released after the last one, so the chunks cost no mapping,
+ * sizing or unmapping of their own (chunks below 8 MiB go through stdio).
  * Anything else done to the stream in between, or its close, first settles
  * the mapping (bulk_settle), trimming the file to what was written when the
  * write stopped early.
@@ -170,7 +171,7 @@ size_t Server::big_fwrite(Stream *st, const void *src, size_t size, size_t nmemb
     const uint64_t min_par = 8ull << 20;
     if (rest < n)
         rest = n;
-    if (!b.m && rest < min_par)
+    if (!b.m && n < min_par)                     /* small chunks: stdio (waking the pool costs more) */
         return fwrite(src, size, nmemb, f);
     if (fflush(f) != 0) {
         bulk_settle(st);
@@ -216,7 +217,9 @@ size_t Server::big_fwrite(Stream *st, const void *src, size_t size, size_t nmemb
         b.orig = sb.st_size;
         b.rfd = rfd;
     }
-    {
+    if (n < (1ull << 20)) {                      /* a short tail of a mapped write */
+        memcpy(b.m + (pos - b.mstart), src, n);
+    } else {
         std::lock_guard<std::mutex> g(pool_mu_);
         if (!pool_)
             pool_.reset(new CopyPool());
