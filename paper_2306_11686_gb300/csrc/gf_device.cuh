@@ -487,10 +487,12 @@ template <class T, int OP, class F> __device__ void tramp_reduce_s1(const gf_reg
 /* kernel split: ask the host to launch the region kernel; its grid, or < 0 */
 static __device__ int64_t split_launch(gf_state *S, int *status);
 
-static __device__ __noinline__ int run_region(gf_state *S)
+/* err: the program's error word, read by the caller before it wrote the
+ * region's descriptor (the read's round trip overlaps those stores) */
+static __device__ __noinline__ int run_region(gf_state *S, int32_t err)
 {
-    if (*(volatile int32_t *)&S->error)      /* after a timeout the workers may still be busy */
-        return S->error;
+    if (err)                                  /* after a timeout the workers may still be busy */
+        return err;
     atomicAdd((unsigned long long *)&S->st_regions, 1ull);   /* no result needed: no round trip */
     if (S->split) {
         /* the paper's kernel split (Sec. 3.3, Fig. 3): one RPC per region, on
@@ -612,6 +614,7 @@ __device__ int gf_parallel_for(int64_t b, int64_t e, int sched, int64_t chunk, F
     if (e <= b)
         return GF_OK;
     gf_state *S = gfd::s_st;
+    const int32_t err = *(volatile int32_t *)&S->error;   /* read first: its round trip overlaps the stores below */
     gf_region *r = &S->region;
     r->fn = gfd::static1_fits(sched, chunk, b, e) ? (uint64_t)(&gfd::tramp_for_s1<F>) : (uint64_t)(&gfd::tramp_for<F>);
     r->b = b;
@@ -620,7 +623,7 @@ __device__ int gf_parallel_for(int64_t b, int64_t e, int sched, int64_t chunk, F
     r->sched = sched;
     r->red = GF_RED_NONE;
     gfd::put_body(r, body);
-    return gfd::run_region(S);
+    return gfd::run_region(S, err);
 }
 
 /* Worksharing reduction: *out = op over body(i), i in [b, e).  T is double or
@@ -637,6 +640,7 @@ __device__ int gf_reduce(int64_t b, int64_t e, int sched, int64_t chunk, F body,
         return GF_OK;
     }
     gf_state *S = gfd::s_st;
+    const int32_t err = *(volatile int32_t *)&S->error;   /* read first: its round trip overlaps the stores below */
     gf_region *r = &S->region;
     r->fn = gfd::static1_fits(sched, chunk, b, e) ? (uint64_t)(&gfd::tramp_reduce_s1<T, OP, F>)
                                                   : (uint64_t)(&gfd::tramp_reduce<T, OP, F>);
@@ -646,7 +650,7 @@ __device__ int gf_reduce(int64_t b, int64_t e, int sched, int64_t chunk, F body,
     r->sched = sched;
     r->red = OP;
     gfd::put_body(r, body);
-    int rc = gfd::run_region(S);
+    int rc = gfd::run_region(S, err);
     gfd::acc<T, OP> a;
     a.from_words((const uint64_t *)S->red_result);
     *out = a.result();
@@ -735,6 +739,7 @@ __device__ int gf_parallel_for_batch(int nloops, const int64_t *trips, int64_t *
     if (acc == 0)
         return GF_OK;
     gf_state *S = gfd::s_st;
+    const int32_t err = *(volatile int32_t *)&S->error;   /* read first: its round trip overlaps the stores below */
     gf_region *r = &S->region;
     gfd::batch_body<F> bb{nloops, trips, prefix, chunk, body};
     r->fn = (uint64_t)(&gfd::tramp_batch<F>);
@@ -744,7 +749,7 @@ __device__ int gf_parallel_for_batch(int nloops, const int64_t *trips, int64_t *
     r->sched = sched;
     r->red = GF_RED_NONE;
     gfd::put_body(r, bb);
-    return gfd::run_region(S);
+    return gfd::run_region(S, err);
 }
 
 /* Barrier across every worker of the grid (paper Sec. 3.3: `omp barrier`

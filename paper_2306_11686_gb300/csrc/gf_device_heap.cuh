@@ -373,14 +373,18 @@ static __device__ __forceinline__ void *gf_malloc_body(size_t n)
     gf_state *S = gfd::s_st;
     gf_heap *H = &S->heap;
     if (n > GF_HEAP_MAX_SMALL) {
+        const unsigned long long pb = ((unsigned long long)n + (1ull << GF_PAGE_SHIFT) - 1) &
+                                      ~((1ull << GF_PAGE_SHIFT) - 1);   /* whole pages, as free counts them */
+        /* counted before the allocation, so this atomic's round trip overlaps
+         * the allocation's own (taken back if it fails; a concurrent failed
+         * request can then show in another's high-water reading) */
+        const unsigned long long live = atomicAdd((unsigned long long *)&H->live_bytes, pb) + pb;
         void *p = gfd::large_malloc(H, n, S->timeout_ns);
         atomicAdd((unsigned long long *)(p ? &H->n_alloc : &H->n_fail), 1ull);
-        if (p) {
-            const unsigned long long pb = ((unsigned long long)n + (1ull << GF_PAGE_SHIFT) - 1) &
-                                          ~((1ull << GF_PAGE_SHIFT) - 1);   /* whole pages, as free counts them */
-            const unsigned long long live = atomicAdd((unsigned long long *)&H->live_bytes, pb) + pb;
+        if (p)
             atomicMax((unsigned long long *)&H->high_water, live);
-        }
+        else
+            atomicAdd((unsigned long long *)&H->live_bytes, 0ull - pb);
         return p;
     }
     const uint32_t cls = gfd::size_class(n ? n : 1);
