@@ -180,12 +180,13 @@ GF_MAIN(rpc_timeout)(int argc, char **argv)
 }
 
 /*
- * main_printf_batch          buffers: 0 = int64 results[8]
+ * main_printf_batch [path]   buffers: 0 = int64 results[8]
  * The initial thread's buffered printf: 100 lines of one format (three full
  * batches and a partial one), a line of another format with a string, a
  * result read in its own statement, a non-printf call (clock) in between, a
  * record too large for the buffer, 40 lines of a third format, a result
- * read only after a later call (-1 by contract), then main returns with
+ * read only after a later call (-1 by contract), 50 buffered fprintf lines
+ * to a file closed right after them (path given), then main returns with
  * records still buffered.  Every line must appear once, in program order.
  */
 GF_MAIN(main_printf_batch)(int argc, char **argv)
@@ -208,6 +209,14 @@ GF_MAIN(main_printf_batch)(int argc, char **argv)
         gf_printf("d %d %.17g\n", k, k * 0.25);
     res[3] = gf_clock() >= 0 ? 1 : 0;
     res[4] = (int)late;                                   /* its batch already went: -1 */
+    if (argc > 1) {                                       /* buffered fprintf, then fclose at once */
+        GF_FILE f = gf_fopen(argv[1], "w");
+        if (!f)
+            return 3;
+        for (int k = 0; k < 50; k++)
+            gf_fprintf(f, "f %d %s\n", k, "x");
+        res[5] = gf_fclose(f);
+    }
     gf_printf("e %d\n", 1);
     gf_printf("e %d\n", 2);                              /* left buffered when main returns */
     return 0;

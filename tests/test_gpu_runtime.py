@@ -448,14 +448,15 @@ def test_main_printf_buffered(gf_lib, tmp_path):
     gf = gf_lib
     res = torch.zeros(8, dtype=torch.int64, device="cuda")
     with gf.Context(timeout_ns=10_000_000_000, stdout_path=tmp_path / "out.txt", heap_bytes=64 << 20) as c:
-        rc, ec = c.run("main_printf_batch", [], [(res, 1)])
+        rc, ec = c.run("main_printf_batch", [tmp_path / "f.txt"], [(res, 1)])
         st = c.stats()
     assert ec == 0
+    assert open(tmp_path / "f.txt").read().splitlines() == [f"f {k} x" for k in range(50)] and res[5].item() == 0
     big = "".join(chr(ord("a") + k % 26) for k in range(1399))
     want = [f"a {k}" for k in range(100)] + ["b str -1", "c 7", "big " + big]
     want += ["d %d %.17g" % (k, 0.5 if k == 0 else k * 0.25) for k in range(40)] + ["e 1", "e 2"]
     assert open(tmp_path / "out.txt").read().splitlines() == want
     r = res.cpu().tolist()
     assert r[0] == 4 and r[1] == 1 and r[2] == len("big ") + 1399 + 1 and r[3] == 1 and r[4] == -1
-    assert st.rpc_calls[gf.OP_PRINTF] == len(want)
-    assert st.rpc_slots[gf.OP_PRINTF] <= 14                # 145 calls in at most 14 slots
+    assert st.rpc_calls[gf.OP_PRINTF] == len(want) + 50
+    assert st.rpc_slots[gf.OP_PRINTF] <= 17                # 195 calls in at most 17 slots
