@@ -21,6 +21,120 @@ static __device__ __forceinline__ uint64_t serve_mix(uint64_t z)
     return z ^ (z >> 31);
 }
 
+/* one row's sum, y_i = sum of val_j x[col_j] in CSR order, one rounding
+ * each, as in the serial program; values and columns read two at a time
+ * (16-byte and 8-byte loads from an even index), the gathers of eight
+ * nonzeros in flight together.  The matrix is constant for the whole
+ * program (read-only loads); x was written by the previous pass, so it
+ * takes ordinary loads. */
+static __device__ __forceinline__ double spmv_row(const long long *rowptr, const int *col, const double *val,
+                                                  const double *xs, bool vec, long long i)
+{
+    double s = 0.0;
+    const long long j0 = __ldg(rowptr + i), j1 = __ldg(rowptr + i + 1);
+    long long j = j0;
+    if (vec) {
+        if ((j & 1) && j < j1) {
+            s = s + __ldg(val + j) * xs[__ldg(col + j)];
+            j++;
+        }
+#pragma unroll 4
+        for (; j + 1 < j1; j += 2) {
+            const double2 v = __ldg((const double2 *)(val + j));
+            const int2 c = __ldg((const int2 *)(col + j));
+            const double x0 = xs[c.x], x1 = xs[c.y];
+            s = s + v.x * x0;
+            s = s + v.y * x1;
+        }
+    }
+#pragma unroll 8
+    for (; j < j1; j++)
+        s = s + __ldg(val + j) * xs[__ldg(col + j)];
+    return s;
+}
+
+/* two rows' sums side by side (each in its own CSR order) when both start
+ * at an even index and have the same length, which lets their loads and
+ * gathers overlap; any other pair row by row */
+static __device__ __forceinline__ void spmv_rows2(const long long *rowptr, const int *col, const double *val,
+                                                  const double *xs, bool vec, long long i0, long long i1,
+                                                  double *s0, double *s1)
+{
+    const long long a0 = __ldg(rowptr + i0), e0 = __ldg(rowptr + i0 + 1);
+    const long long a1 = __ldg(rowptr + i1), e1 = __ldg(rowptr + i1 + 1);
+    const long long len = e0 - a0;
+    if (!vec || (a0 & 1) || (a1 & 1) || e1 - a1 != len) {
+        *s0 = spmv_row(rowptr, col, val, xs, vec, i0);
+        *s1 = spmv_row(rowptr, col, val, xs, vec, i1);
+        return;
+    }
+    double t0 = 0.0, t1 = 0.0;
+    long long k = 0;
+#pragma unroll 4
+    for (; k + 1 < len; k += 2) {
+        const double2 v0 = __ldg((const double2 *)(val + a0 + k)), v1 = __ldg((const double2 *)(val + a1 + k));
+        const int2 c0 = __ldg((const int2 *)(col + a0 + k)), c1 = __ldg((const int2 *)(col + a1 + k));
+        const double x00 = xs[c0.x], x01 = xs[c0.y], x10 = xs[c1.x], x11 = xs[c1.y];
+        t0 = t0 + v0.x * x00;
+        t0 = t0 + v0.y * x01;
+        t1 = t1 + v1.x * x10;
+        t1 = t1 + v1.y * x11;
+    }
+    if (k < len) {
+        t0 = t0 + __ldg(val + a0 + k) * xs[__ldg(col + a0 + k)];
+        t1 = t1 + __ldg(val + a1 + k) * xs[__ldg(col + a1 + k)];
+    }
+    *s0 = t0;
+    *s1 = t1;
+}
+
+/* the libc requests of row i in pass rr (all of them after its sum, as in
+ * the serial program) */
+static __device__ __noinline__ void serve_requests(const long long *req, long long *res, const unsigned *mark,
+                                                   long long qa, long long qb, unsigned prog, int rr, long long i,
+                                                   double s, GF_FILE f)
+{
+    if (!((mark[i >> 5] >> (i & 31)) & 1u))
+        return;
+    const long long key = ((long long)rr << 32) | (long long)i;
+    long long lo = qa, hi = qb;                 /* first request with key >= (pass, row) */
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (req[2 * mid] < key)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    for (long long q = lo; q < qb && req[2 * q] == key; q++) {
+        const int kind = (int)(req[2 * q + 1] & 0xff);
+        const unsigned size = (unsigned)(req[2 * q + 1] >> 8);
+        if (kind == 0) {
+            const unsigned long long words = (size + 7) / 8;
+            unsigned long long *b = (unsigned long long *)gf_malloc(16 + 8 * words);
+            if (!b) {
+                res[q] = -2;
+                continue;
+            }
+            b[0] = (unsigned long long)prog | ((unsigned long long)rr << 32);
+            b[1] = (unsigned long long)i | ((unsigned long long)size << 32);
+            const uint64_t k0 = serve_mix(((uint64_t)prog << 40) ^ ((uint64_t)rr << 32) ^ (uint64_t)i);
+            for (unsigned long long w = 0; w < words; w++)
+                b[2 + w] = serve_mix(k0 + w * 0x9E3779B97F4A7C15ull);
+            res[q] = (long long)gf_fwrite(b, 1, 16 + (size_t)size, f);
+            gf_free(b);
+        } else if (kind == 1) {
+            res[q] = gf_printf("p %d r %d row %d y %.17g\n", (int)prog, rr, (int)i, s);
+        } else if (kind == 2) {
+            res[q] = gf_clock();
+        } else {
+            char name[16] = "GF_SERVE_VAR0";
+            name[12] = (char)('0' + (int)(i % 3));
+            const char *v = gf_getenv(name);
+            res[q] = v ? (long long)gf_strlen(v) : -1;
+        }
+    }
+}
+
 /* compiled for 4 resident blocks per SM (64 registers): each of the
  * concurrent instances gets a quarter of the co-resident blocks' worth of
  * warps more for its latency-bound gathers (measured: 77.0 k vs 72.8 k
@@ -70,73 +184,23 @@ GF_MAIN_BOUNDS(spmv_serve, 4)(int argc, char **argv)
                 atomicOr(&mark[row >> 5], 1u << (row & 31));
             }))
             return 10;
-        const int rc = gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) {
-            double s = 0.0;
-            const long long j0 = __ldg(rowptr + i), j1 = __ldg(rowptr + i + 1);
-            long long j = j0;
-            /* the adds stay in CSR order, one rounding each, as in the serial
-             * program; values and columns of a row are read two at a time
-             * (16-byte and 8-byte loads from an even index), and the gathers
-             * of eight nonzeros are in flight together.  The matrix is
-             * constant for the whole program (read-only loads); x was written
-             * by the previous pass, so it takes ordinary loads */
-            if (vec) {
-                if ((j & 1) && j < j1) {
-                    s = s + __ldg(val + j) * xs[__ldg(col + j)];
-                    j++;
-                }
-#pragma unroll 4
-                for (; j + 1 < j1; j += 2) {
-                    const double2 v = __ldg((const double2 *)(val + j));
-                    const int2 c = __ldg((const int2 *)(col + j));
-                    const double x0 = xs[c.x], x1 = xs[c.y];
-                    s = s + v.x * x0;
-                    s = s + v.y * x1;
-                }
-            }
-#pragma unroll 8
-            for (; j < j1; j++)
-                s = s + __ldg(val + j) * xs[__ldg(col + j)];
-            ys[i] = s;
-            if (qa == qb || !((mark[i >> 5] >> (i & 31)) & 1u))
+        const long long half = (n + 1) / 2;
+        const int rc = gf_parallel_for(0, half, GF_SCHED_STATIC, 1, [=](int64_t p) {
+            /* rows p and p + half: two independent sums in flight per thread */
+            const long long i0 = p, i1 = p + half;
+            double s0, s1 = 0.0;
+            if (i1 < n)
+                spmv_rows2(rowptr, col, val, xs, vec, i0, i1, &s0, &s1);
+            else
+                s0 = spmv_row(rowptr, col, val, xs, vec, i0);
+            ys[i0] = s0;
+            if (i1 < n)
+                ys[i1] = s1;
+            if (qa == qb)
                 return;
-            const long long key = ((long long)rr << 32) | (long long)i;
-            long long lo = qa, hi = qb;                 /* first request with key >= (pass, row) */
-            while (lo < hi) {
-                const long long mid = (lo + hi) >> 1;
-                if (req[2 * mid] < key)
-                    lo = mid + 1;
-                else
-                    hi = mid;
-            }
-            for (long long q = lo; q < qb && req[2 * q] == key; q++) {
-                const int kind = (int)(req[2 * q + 1] & 0xff);
-                const unsigned size = (unsigned)(req[2 * q + 1] >> 8);
-                if (kind == 0) {
-                    const unsigned long long words = (size + 7) / 8;
-                    unsigned long long *b = (unsigned long long *)gf_malloc(16 + 8 * words);
-                    if (!b) {
-                        res[q] = -2;
-                        continue;
-                    }
-                    b[0] = (unsigned long long)prog | ((unsigned long long)rr << 32);
-                    b[1] = (unsigned long long)i | ((unsigned long long)size << 32);
-                    const uint64_t k0 = serve_mix(((uint64_t)prog << 40) ^ ((uint64_t)rr << 32) ^ (uint64_t)i);
-                    for (unsigned long long w = 0; w < words; w++)
-                        b[2 + w] = serve_mix(k0 + w * 0x9E3779B97F4A7C15ull);
-                    res[q] = (long long)gf_fwrite(b, 1, 16 + (size_t)size, f);
-                    gf_free(b);
-                } else if (kind == 1) {
-                    res[q] = gf_printf("p %d r %d row %d y %.17g\n", (int)prog, rr, (int)i, s);
-                } else if (kind == 2) {
-                    res[q] = gf_clock();
-                } else {
-                    char name[16] = "GF_SERVE_VAR0";
-                    name[12] = (char)('0' + (int)(i % 3));
-                    const char *v = gf_getenv(name);
-                    res[q] = v ? (long long)gf_strlen(v) : -1;
-                }
-            }
+            serve_requests(req, res, mark, qa, qb, prog, rr, i0, s0, f);
+            if (i1 < n)
+                serve_requests(req, res, mark, qa, qb, prog, rr, i1, s1, f);
         });
         if (rc)
             return 10;
