@@ -53,41 +53,6 @@ static __device__ __forceinline__ double spmv_row(const long long *rowptr, const
     return s;
 }
 
-/* two rows' sums side by side (each in its own CSR order) when both start
- * at an even index and have the same length, which lets their loads and
- * gathers overlap; any other pair row by row */
-static __device__ __forceinline__ void spmv_rows2(const long long *rowptr, const int *col, const double *val,
-                                                  const double *xs, bool vec, long long i0, long long i1,
-                                                  double *s0, double *s1)
-{
-    const long long a0 = __ldg(rowptr + i0), e0 = __ldg(rowptr + i0 + 1);
-    const long long a1 = __ldg(rowptr + i1), e1 = __ldg(rowptr + i1 + 1);
-    const long long len = e0 - a0;
-    if (!vec || (a0 & 1) || (a1 & 1) || e1 - a1 != len) {
-        *s0 = spmv_row(rowptr, col, val, xs, vec, i0);
-        *s1 = spmv_row(rowptr, col, val, xs, vec, i1);
-        return;
-    }
-    double t0 = 0.0, t1 = 0.0;
-    long long k = 0;
-#pragma unroll 4
-    for (; k + 1 < len; k += 2) {
-        const double2 v0 = __ldg((const double2 *)(val + a0 + k)), v1 = __ldg((const double2 *)(val + a1 + k));
-        const int2 c0 = __ldg((const int2 *)(col + a0 + k)), c1 = __ldg((const int2 *)(col + a1 + k));
-        const double x00 = xs[c0.x], x01 = xs[c0.y], x10 = xs[c1.x], x11 = xs[c1.y];
-        t0 = t0 + v0.x * x00;
-        t0 = t0 + v0.y * x01;
-        t1 = t1 + v1.x * x10;
-        t1 = t1 + v1.y * x11;
-    }
-    if (k < len) {
-        t0 = t0 + __ldg(val + a0 + k) * xs[__ldg(col + a0 + k)];
-        t1 = t1 + __ldg(val + a1 + k) * xs[__ldg(col + a1 + k)];
-    }
-    *s0 = t0;
-    *s1 = t1;
-}
-
 /* the libc requests of row i in pass rr (all of them after its sum, as in
  * the serial program) */
 static __device__ __noinline__ void serve_requests(const long long *req, long long *res, const unsigned *mark,
@@ -184,23 +149,15 @@ GF_MAIN_BOUNDS(spmv_serve, 4)(int argc, char **argv)
                 atomicOr(&mark[row >> 5], 1u << (row & 31));
             }))
             return 10;
-        const long long half = (n + 1) / 2;
-        const int rc = gf_parallel_for(0, half, GF_SCHED_STATIC, 1, [=](int64_t p) {
-            /* rows p and p + half: two independent sums in flight per thread */
-            const long long i0 = p, i1 = p + half;
-            double s0, s1 = 0.0;
-            if (i1 < n)
-                spmv_rows2(rowptr, col, val, xs, vec, i0, i1, &s0, &s1);
-            else
-                s0 = spmv_row(rowptr, col, val, xs, vec, i0);
-            ys[i0] = s0;
-            if (i1 < n)
-                ys[i1] = s1;
+        /* the row loop keeps only the sum; the requests (malloc, record
+         * generation, RPC) live out of line, so their code and registers
+         * stay out of the loop over the nonzeros */
+        const int rc = gf_parallel_for(0, n, GF_SCHED_STATIC, 1, [=](int64_t i) {
+            const double s = spmv_row(rowptr, col, val, xs, vec, i);
+            ys[i] = s;
             if (qa == qb)
                 return;
-            serve_requests(req, res, mark, qa, qb, prog, rr, i0, s0, f);
-            if (i1 < n)
-                serve_requests(req, res, mark, qa, qb, prog, rr, i1, s1, f);
+            serve_requests(req, res, mark, qa, qb, prog, rr, i, s, f);
         });
         if (rc)
             return 10;
