@@ -67,6 +67,27 @@ GF_MAIN_BOUNDS(loops, 8)(int argc, char **argv)
  *                                 (heap blocks not granted or corrupted)
  * mode 0: one region per loop; mode 1: one batched region.
  */
+/* the libc part of an iteration (every 4096th), out of line so that its
+ * code and registers stay out of the loop every other iteration runs */
+static __device__ __noinline__ double loop_rpc_libc(int k, int64_t i, double v, unsigned long long *fails)
+{
+    const unsigned long long words = (64ull << (k & 7)) / 8;
+    double *w = (double *)gf_malloc(words * 8);
+    if (!w) {
+        atomicAdd(fails, 1ull);
+    } else {
+        w[0] = v;
+        w[words - 1] = -v;
+        const double r = w[0];
+        if (w[words - 1] != -r)
+            atomicAdd(fails, 1ull);
+        v = r;
+        gf_free(w);
+    }
+    gf_printf("%d %lld %.17g\n", k, (long long)i, v);
+    return v;
+}
+
 struct loop_rpc_body {
     const double *x, *y;
     double *z;
@@ -74,22 +95,8 @@ struct loop_rpc_body {
     __device__ __forceinline__ void operator()(int k, double a, long long o, int64_t i) const
     {
         double v = a * x[o + i] + y[o + i];
-        if ((i & 4095) == 0) {
-            const unsigned long long words = (64ull << (k & 7)) / 8;
-            double *w = (double *)gf_malloc(words * 8);
-            if (!w) {
-                atomicAdd(fails, 1ull);
-            } else {
-                w[0] = v;
-                w[words - 1] = -v;
-                const double r = w[0];
-                if (w[words - 1] != -r)
-                    atomicAdd(fails, 1ull);
-                v = r;
-                gf_free(w);
-            }
-            gf_printf("%d %lld %.17g\n", k, (long long)i, v);
-        }
+        if ((i & 4095) == 0)
+            v = loop_rpc_libc(k, i, v, fails);
         z[o + i] = v;
     }
 };
