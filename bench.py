@@ -222,8 +222,9 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20,
+                    help="timed programs (20 x 22 ms: long enough for several clock samples)")
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gf", choices=["gf", "reference"])
     ap.add_argument("--ref-sweeps", type=int, default=4)
     ap.add_argument("--cpu-sweeps", type=int, default=8)
