@@ -18,6 +18,7 @@
  *   fmtcache   the format ships once; later slots carry only its key
  *   bulkfile   large fwrites from the bulk arena between small inline ones
  *   bulkchunks large fwrites in chunks mapped once, and writes cut short
+ *   closerace  fclose while other producers write and flush the same file
  */
 #include <stdio.h>
 #include <stdlib.h>
@@ -243,7 +244,7 @@ int main(int argc, char **argv)
         return 2;
     const std::string sc = argv[1];
     FILE *out = fopen(argv[2], "w");
-    int nthreads = sc == "threads" ? 4 : 1;
+    int nthreads = sc == "threads" || sc == "closerace" ? 4 : 1;
     Ring R(sc == "basic" || sc == "dead" ? 8 : 64, 4096);
     ServerRun S;
     S.srv.set_stdout(out);
@@ -408,6 +409,54 @@ int main(int argc, char **argv)
                 memcmp(got.data() + pre + 4 + len, arena.data(), len) ||
                 memcmp(got.data() + pre + 4 + 2 * len, "TAIL", 4))
                 return fail(mode);
+        }
+        remove(path.c_str());
+        S.join();
+        fclose(out);
+    } else if (sc == "closerace") {
+        /* a file closed while other producers keep writing to it and
+         * flushing it through other server threads: every call returns (a
+         * write after the close fails), nothing crashes, and the file holds
+         * whole records only */
+        const std::string path = std::string(argv[2]) + ".race";
+        for (int round = 0; round < 20; round++) {
+            const int64_t fh = call1(R, GF_OP_FOPEN, {{'s', 0, path + '\0'}, {'s', 0, std::string("wb") + '\0'}});
+            if (!fh)
+                return fail("fopen");
+            std::atomic<bool> closed{false};
+            std::atomic<int> bad{0};
+            std::vector<std::thread> ps;
+            for (int p = 0; p < 3; p++)
+                ps.emplace_back([&, p] {
+                    for (int k = 0; k < 200; k++) {
+                        const int64_t w = call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', 8, ""}, {'L', (uint64_t)fh, ""},
+                                                                  {'b', 0, std::string("rec0123\n")}});
+                        if (w != 8 && !closed.load())
+                            bad++;
+                        if (k % 50 == 0)
+                            call1(R, GF_OP_FFLUSH, {{'L', (uint64_t)fh, ""}});
+                    }
+                    (void)p;
+                });
+            std::this_thread::sleep_for(std::chrono::microseconds(200 * (round % 5)));
+            closed = true;
+            const int64_t rc = call1(R, GF_OP_FCLOSE, {{'L', (uint64_t)fh, ""}});
+            for (auto &t : ps)
+                t.join();
+            if (rc != 0 || bad)
+                return fail("close race");
+            if (call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', 8, ""}, {'L', (uint64_t)fh, ""},
+                                        {'b', 0, std::string("late000\n")}}) != 0)
+                return fail("write after close");
+            FILE *in = fopen(path.c_str(), "rb");
+            std::string got(1 << 16, '\0');
+            got.resize(fread(&got[0], 1, got.size(), in));
+            fclose(in);
+            if (got.size() % 8)
+                return fail("torn record");
+            for (size_t o = 0; o < got.size(); o += 8)
+                if (got.compare(o, 8, "rec0123\n"))
+                    return fail("record content");
         }
         remove(path.c_str());
         S.join();
