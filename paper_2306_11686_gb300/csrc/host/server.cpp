@@ -63,8 +63,18 @@ class CopyPool {
   public:
     CopyPool()
     {
+        /* page faults of distinct pages run in parallel; two cores are left
+         * to the server thread and the host thread waiting on the program
+         * (on a 16-core host a 128 MiB write took 1.91 ms with 14 copy
+         * threads, 2.22-2.27 with 16, 1.95 with 12, 2.31 with 8) */
         const unsigned hw = std::thread::hardware_concurrency();
-        nthr_ = hw < 4 ? 4 : hw > 16 ? 16 : hw;       /* page faults of distinct pages run in parallel */
+        const unsigned n = hw > 2 ? hw - 2 : 1;
+        nthr_ = n < 4 ? 4 : n > 16 ? 16 : n;
+        if (const char *e = getenv("GF_COPY_THREADS")) {  /* a fixed count, for measurement */
+            const int v = atoi(e);
+            if (v >= 1 && v <= 64)
+                nthr_ = (unsigned)v;
+        }
         for (unsigned t = 0; t < nthr_; t++)
             th_.emplace_back([this, t] { loop(t); });
     }
