@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <condition_variable>
+#include <deque>
 #include <thread>
 #include <chrono>
 #include <vector>
@@ -140,6 +141,66 @@ class CopyPool {
 };
 
 /*
+ * Releases the file mappings of finished large writes on a thread of its
+ * own.  Unmapping a shared mapping walks every page it covers (dirty state,
+ * reverse map); the bytes are in the page cache already, so the writer's
+ * reply, a reopen or a read of the file need not wait for it.  Started on
+ * first use; its destructor releases what is still queued.
+ */
+class Unmapper {
+  public:
+    ~Unmapper()
+    {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            stop_ = true;
+        }
+        cv_.notify_one();
+        if (th_.joinable())
+            th_.join();
+    }
+    void put(void *m, size_t len, int fd)
+    {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            q_.push_back({m, len, fd});
+            if (!th_.joinable())
+                th_ = std::thread([this] { loop(); });
+        }
+        cv_.notify_one();
+    }
+
+  private:
+    struct Job {
+        void *m;
+        size_t len;
+        int fd;
+    };
+    void loop()
+    {
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            cv_.wait(lk, [this] { return stop_ || !q_.empty(); });
+            while (!q_.empty()) {                /* queued work is done before stopping */
+                const Job j = q_.front();
+                q_.pop_front();
+                lk.unlock();
+                munmap(j.m, j.len);
+                close(j.fd);
+                lk.lock();
+            }
+            if (stop_)
+                return;
+        }
+    }
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::deque<Job> q_;
+    bool stop_ = false;
+    std::thread th_;
+};
+
+/*
  * fwrite of a large buffer.  A single write(2) to one file copies into the
  * page cache on one thread (the kernel serialises writers of a file), which
  * is the bottleneck for a 128 MiB write.  For a regular file not opened for
@@ -155,8 +216,25 @@ class CopyPool {
  * sizing or unmapping of their own (chunks below 8 MiB go through stdio).
  * Anything else done to the stream in between, or its close, first settles
  * the mapping (bulk_settle), trimming the file to what was written when the
- * write stopped early.
+ * write stopped early.  The mapping of a write that completed is released
+ * by the Unmapper after the reply (bulk_retire).
  */
+void Server::bulk_retire(Stream *st)
+{
+    Stream::Bulk &b = st->bulk;
+    if (!b.m || b.next < b.end) {
+        bulk_settle(st);
+        return;
+    }
+    {
+        std::lock_guard<std::mutex> g(pool_mu_);
+        if (!unmap_)
+            unmap_.reset(new Unmapper());
+        unmap_->put(b.m, b.mlen, b.rfd);
+    }
+    b = Stream::Bulk();
+}
+
 void Server::bulk_settle(Stream *st)
 {
     Stream::Bulk &b = st->bulk;
@@ -236,9 +314,8 @@ size_t Server::big_fwrite(Stream *st, const void *src, size_t size, size_t nmemb
         pool_->copy(b.m + (pos - b.mstart), (const unsigned char *)src, n);
     }
     b.next = pos + (int64_t)n;
-    const bool last = b.next >= b.end;
-    if (last)
-        bulk_settle(st);
+    if (b.next >= b.end)
+        bulk_retire(st);
     if (fseeko(f, pos + (off_t)n, SEEK_SET) != 0)
         return 0;
     return nmemb;

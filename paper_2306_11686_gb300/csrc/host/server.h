@@ -154,6 +154,7 @@ struct HostStats {
 };
 
 class CopyPool;
+class Unmapper;
 
 /* A stdio stream whose bytes a thread of its own writes to the file: a write
  * through the stream only queues the bytes (the stream is unbuffered, so
@@ -228,8 +229,10 @@ class Server {
     std::mutex user_mu_;
     std::map<uint32_t, std::pair<user_fn, void *>> user_;
     std::unique_ptr<CopyPool> pool_;   /* copy threads of large writes, started on first use */
+    std::unique_ptr<Unmapper> unmap_;  /* releases the mappings of finished large writes */
     size_t big_fwrite(Stream *st, const void *src, size_t size, size_t nmemb, uint64_t rest);
     void bulk_settle(Stream *st);
+    void bulk_retire(Stream *st);
 };
 
 /* record accessors (shared with tests) */
