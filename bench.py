@@ -436,7 +436,9 @@ def main():
                                           "printf": round(st.rpc_wait_op_ns[gf.OP_PRINTF] / 1e6, 3),
                                           "fwrite": round(st.rpc_wait_op_ns[gf.OP_FWRITE] / 1e6, 3),
                                           "fopen_fclose": round((st.rpc_wait_op_ns[gf.OP_FOPEN] +
-                                                                 st.rpc_wait_op_ns[gf.OP_FCLOSE]) / 1e6, 3)},
+                                                                 st.rpc_wait_op_ns[gf.OP_FCLOSE]) / 1e6, 3),
+                                          "fopen": round(st.rpc_wait_op_ns[gf.OP_FOPEN] / 1e6, 3),
+                                          "fclose": round(st.rpc_wait_op_ns[gf.OP_FCLOSE] / 1e6, 3)},
                                       "rpc_client": round(st.rpc_client_ns / 1e6, 3),
                                       "serial_heap": round(st.heap_ns / 1e6, 3),
                                       "rest": round((st.main_ns - st.region_ns - st.rpc_wait_ns - st.heap_ns -
