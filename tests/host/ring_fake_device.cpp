@@ -527,6 +527,23 @@ int main(int argc, char **argv)
                 return fail(mode);
             }
         }
+        /* every mapping of the file is gone: the finished writes' ones are
+         * released after their replies, on the server's unmap thread */
+        bool mapped = true;
+        for (int tries = 0; tries < 200 && mapped; tries++) {
+            mapped = false;
+            FILE *mp = fopen("/proc/self/maps", "r");
+            char line[4096];
+            while (mp && fgets(line, sizeof line, mp))
+                if (strstr(line, path.c_str()))
+                    mapped = true;
+            if (mp)
+                fclose(mp);
+            if (mapped)
+                std::this_thread::sleep_for(std::chrono::milliseconds(10));
+        }
+        if (mapped)
+            return fail("the written file is still mapped");
         remove(path.c_str());
         S.join();
         fclose(out);
