@@ -731,12 +731,8 @@ static __device__ int copy_region_body(void *dst, const void *src, uint64_t byte
  * (pinned, device-mapped host memory, two halves): the grid copies chunk c
  * into one half while the host writes chunk c-1 from the other; chunk c is
  * posted only after chunk c-1 has been written, so the file sees the chunks
- * in order.  No host-side CUDA call is involved.  The host is the slower
- * side, so only the first chunk's copy is not overlapped: it is kept to
- * GF_BULK_FIRST bytes (the size from which the host maps the file for the
- * whole write), the later ones fill a half each.
+ * in order.  No host-side CUDA call is involved.
  */
-#define GF_BULK_FIRST (8ull << 20)
 static __device__ __noinline__ size_t fwrite_bulk(const void *buf, size_t size, size_t n, GF_FILE f)
 {
     gf_state *S = s_st;
@@ -746,9 +742,8 @@ static __device__ __noinline__ size_t fwrite_bulk(const void *buf, size_t size, 
     unsigned long long tk = 0;
     bool pend = false, ok = true;
     int k = 0;
-    for (uint64_t off = 0, len = 0; off < bytes && ok; off += len, k ^= 1) {
-        const uint64_t cap = off == 0 && half > GF_BULK_FIRST ? GF_BULK_FIRST : half;
-        len = bytes - off < cap ? bytes - off : cap;
+    for (uint64_t off = 0; off < bytes && ok; off += half, k ^= 1) {
+        const uint64_t len = bytes - off < half ? bytes - off : half;
         if (copy_region(arena + (uint64_t)k * half, (const uint8_t *)buf + off, len) != GF_OK)
             ok = false;
         if (pend) {
