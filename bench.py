@@ -35,10 +35,11 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 operations of the serial program per interior point: 5 neighbour adds,
 # the division by 6, the residual's subtract.
 FP64_OPS_PER_POINT = 7
-# DRAM bytes (read + write) of one full launch, scaled from an ncu capture of
-# the current program kernel (20 sweeps, no final write: 3.1817 + 3.0988 GB,
-# 314.03 MB per sweep) to 100 sweeps plus the final fwrite's 134.2 MB read.
-TRAFFIC_PER_LAUNCH = 100 * 314_025_370 + 134_217_728
+# DRAM bytes (read + write) of one full launch (100 sweeps and the final
+# fwrite), from an ncu capture of the current program kernel on this
+# workload: dram__bytes_read.sum 16.047640 GB + dram__bytes_write.sum
+# 15.610922 GB.
+TRAFFIC_PER_LAUNCH = 16_047_640_000 + 15_610_922_000
 
 
 def fp64_pipe_ops_per_point(int_adds):
