@@ -22,12 +22,14 @@
 #include <stdio.h>
 #include <string.h>
 #include <atomic>
+#include <chrono>
 #include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <set>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -154,7 +156,6 @@ struct HostStats {
 };
 
 class CopyPool;
-class Unmapper;
 
 /* A stdio stream whose bytes a thread of its own writes to the file: a write
  * through the stream only queues the bytes (the stream is unbuffered, so
@@ -182,8 +183,11 @@ class Server {
      * of `nthreads`; returns the number of slots served */
     int poll(Segment &seg, uint32_t tid, uint32_t nthreads);
 
-    /* close FILE*s the programs left open */
+    /* close FILE*s the programs left open (and release retired mappings) */
     void close_all();
+    /* a server thread with nothing to serve calls this: it releases the
+     * mappings of the large writes it served once it has been idle a while */
+    void idle();
     HostStats stats;
 
     /* one landing pad: exposed for tests that decode a record by hand */
@@ -229,7 +233,18 @@ class Server {
     std::mutex user_mu_;
     std::map<uint32_t, std::pair<user_fn, void *>> user_;
     std::unique_ptr<CopyPool> pool_;   /* copy threads of large writes, started on first use */
-    std::unique_ptr<Unmapper> unmap_;  /* releases the mappings of finished large writes */
+    /* mappings of finished large writes, released later by idle() */
+    struct Retired {
+        void *m;
+        size_t len;
+        int fd;
+        std::thread::id owner;       /* the server thread that served the write */
+        std::chrono::steady_clock::time_point t;
+    };
+    std::mutex ret_mu_;
+    std::vector<Retired> retired_;
+    std::atomic<uint32_t> n_retired_{0};
+    void release_retired();
     size_t big_fwrite(Stream *st, const void *src, size_t size, size_t nmemb, uint64_t rest);
     void bulk_settle(Stream *st);
     void bulk_retire(Stream *st);

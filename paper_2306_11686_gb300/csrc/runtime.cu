@@ -307,6 +307,7 @@ static void server_main(gf_ctx *c, uint32_t tid, uint32_t nthr)
             idle = 0;
             continue;
         }
+        c->server.idle();                       /* mappings of this thread's finished writes */
         if (c->nactive.load(std::memory_order_acquire) == 0) {
             std::unique_lock<std::mutex> lk(c->act_mu);
             c->act_cv.wait_for(lk, std::chrono::milliseconds(5),
@@ -928,9 +929,10 @@ extern "C" GF_API int gf_wait(gf_handle *h, int *exit_code, int64_t timeout_ns)
             delete h;
             return GF_ECUDA;
         }
-        if (c->cfg.server_threads == 0)
-            c->server.poll(in->seg, 0, 1);
-        else if (++spins > 256)
+        if (c->cfg.server_threads == 0) {
+            if (!c->server.poll(in->seg, 0, 1))
+                c->server.idle();
+        } else if (++spins > 256)
             std::this_thread::sleep_for(std::chrono::microseconds(20));
         if (timeout_ns > 0 &&
             std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count() >
@@ -1019,8 +1021,8 @@ extern "C" GF_API int gf_rpc_serve(gf_ctx *c, const gf_serve_opts *o)
         bool any = false;
         for (Instance *in : c->inst)
             if (in->seg.active.load(std::memory_order_acquire)) {
-                if (c->cfg.server_threads == 0)
-                    c->server.poll(in->seg, 0, 1);
+                if (c->cfg.server_threads == 0 && !c->server.poll(in->seg, 0, 1))
+                    c->server.idle();
                 if (cudaEventQuery(in->ev_done) == cudaErrorNotReady)
                     any = true;   /* finished programs are collected by gf_wait */
             }

@@ -188,8 +188,10 @@ struct ServerRun {
                         std::this_thread::sleep_for(std::chrono::milliseconds(1));
                         continue;
                     }
-                    if (!srv.poll(R.seg, (uint32_t)k, (uint32_t)n))
+                    if (!srv.poll(R.seg, (uint32_t)k, (uint32_t)n)) {
+                        srv.idle();        /* as the runtime's server threads do */
                         std::this_thread::yield();
+                    }
                 }
             });
     }
@@ -528,7 +530,7 @@ int main(int argc, char **argv)
             }
         }
         /* every mapping of the file is gone: the finished writes' ones are
-         * released after their replies, on the server's unmap thread */
+         * released after their replies, by the serving thread once idle */
         bool mapped = true;
         for (int tries = 0; tries < 200 && mapped; tries++) {
             mapped = false;
