@@ -19,6 +19,8 @@
  *   bulkfile   large fwrites from the bulk arena between small inline ones
  *   bulkchunks large fwrites in chunks mapped once, and writes cut short
  *   closerace  fclose while other producers write and flush the same file
+ *   retire     mappings of finished large writes while no server thread goes
+ *              idle: at most 16 are kept, closing the server releases the rest
  */
 #include <stdio.h>
 #include <stdlib.h>
@@ -176,7 +178,7 @@ static int call(Ring &R, int producer, const std::vector<int> &seqs, std::vector
 struct ServerRun {
     gfh::Server srv;
     std::vector<std::thread> th;
-    std::atomic<bool> stop{false}, pause{false};
+    std::atomic<bool> stop{false}, pause{false}, no_idle{false};
     void start(Ring &R, int n)
     {
         R.seg.reset((uint32_t)n);
@@ -189,7 +191,8 @@ struct ServerRun {
                         continue;
                     }
                     if (!srv.poll(R.seg, (uint32_t)k, (uint32_t)n)) {
-                        srv.idle();        /* as the runtime's server threads do */
+                        if (!no_idle)
+                            srv.idle();    /* as the runtime's server threads do */
                         std::this_thread::yield();
                     }
                 }
@@ -462,6 +465,54 @@ int main(int argc, char **argv)
         }
         remove(path.c_str());
         S.join();
+        fclose(out);
+    } else if (sc == "retire") {
+        S.no_idle = true;
+        const uint64_t C = 8ull << 20;
+        std::vector<uint8_t> arena(C, 0x5a);
+        R.seg.bulk = arena.data();
+        R.seg.bulk_bytes = C;
+        const std::string base = std::string(argv[2]) + ".r";
+        auto maps = [&]() {
+            int n = 0;
+            FILE *mp = fopen("/proc/self/maps", "r");
+            char line[4096];
+            while (mp && fgets(line, sizeof line, mp))
+                if (strstr(line, base.c_str()))
+                    n++;
+            if (mp)
+                fclose(mp);
+            return n;
+        };
+        for (int k = 0; k < 20; k++) {
+            const std::string path = base + std::to_string(k);
+            const int64_t fh = call1(R, GF_OP_FOPEN, {{'s', 0, path + '\0'}, {'s', 0, std::string("wb") + '\0'}});
+            if (!fh)
+                return fail("fopen");
+            if (call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', C, ""}, {'L', (uint64_t)fh, ""}, {'A', 0, ""},
+                                        {'L', C, ""}, {'L', C, ""}}) != (int64_t)C)
+                return fail("fwrite");
+            if (call1(R, GF_OP_FCLOSE, {{'L', (uint64_t)fh, ""}}) != 0)
+                return fail("fclose");
+            if (maps() > 16)
+                return fail("more than 16 finished writes still mapped");
+        }
+        if (maps() != 16)
+            return fail("the 16 latest finished writes are not kept mapped");
+        S.join();                                   /* close_all releases them */
+        if (maps() != 0)
+            return fail("mappings left after close_all");
+        for (int k = 0; k < 20; k++) {
+            const std::string path = base + std::to_string(k);
+            FILE *in = fopen(path.c_str(), "rb");
+            std::vector<uint8_t> got(C + 1);
+            const size_t g = in ? fread(got.data(), 1, got.size(), in) : 0;
+            if (in)
+                fclose(in);
+            remove(path.c_str());
+            if (g != C || memcmp(got.data(), arena.data(), C))
+                return fail("file content");
+        }
         fclose(out);
     } else if (sc == "bulkchunks") {
         /* large writes sent in chunks that name the bytes still to come: the

@@ -22,7 +22,7 @@ def ring_bin(tmp_path_factory):
 
 
 @pytest.mark.parametrize("scenario", ["basic", "aggregate", "ooo", "dead", "stall", "threads", "fmtcache",
-                                      "bulkfile", "bulkchunks", "closerace"])
+                                      "bulkfile", "bulkchunks", "closerace", "retire"])
 def test_ring_scenario(ring_bin, tmp_path, scenario):
     p = subprocess.run([ring_bin, scenario, str(tmp_path / "out.txt")], capture_output=True, text=True, timeout=120)
     assert p.returncode == 0, p.stdout + p.stderr
