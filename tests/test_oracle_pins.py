@@ -287,10 +287,55 @@ def test_synth_oracle_rpc_count(oracle_bin, tmp_path):
     assert out.strip() == f"rpc {want}"
 
 
+def test_synth_oracle_fused_multiply_add_rounds_once(oracle_bin, tmp_path):
+    """fmaf rounds x * 1.0001f + 0.5f once.  For these float32 inputs the
+    product rounded to float32 first gives another result, so a multiply and
+    a separate add would show; the reference is computed exactly in binary64
+    (a 48-bit product plus 0.5 fits in 53 bits, checked with fractions) and
+    rounded once to float32."""
+    from fractions import Fraction
+    x = np.array([7.755090713500977, 15.926447868347168, 15.518893241882324, 15.589431762695312,
+                  7.641292572021484])
+    assert all(_f32(v) == v for v in x)
+    c = _f32(1.0001)
+    want = []
+    for v in x:
+        assert Fraction(v) * Fraction(c) + Fraction(1, 2) == Fraction(v * c + 0.5)   # exact in binary64
+        w = _f32(v * c + 0.5)
+        assert w != _f32(_f32(v * c) + 0.5)                                            # rounding twice differs
+        want.append(w)
+    inputs.write_f64(tmp_path / "x.bin", x)
+    run([oracle_bin("synth"), str(len(x)), "8", "1", "0", "0", "9", tmp_path / "x.bin", tmp_path / "z.bin"])
+    assert np.fromfile(tmp_path / "z.bin").tolist() == want
+
+
+def test_synth_oracle_divergent_iterations(oracle_bin, tmp_path):
+    """The divergent branch is taken where the low 32 bits of the
+    iteration's SplitMix64 output fall below the threshold (the high 32
+    bits decide the RPC): with 1/16 of the iterations divergent, exactly
+    those get the second fused multiply-add."""
+    trip, seed, thresh = 4096, 3, 2 ** 28
+    x = (np.arange(trip) % 7).astype(np.float64)
+    inputs.write_f64(tmp_path / "x.bin", x)
+    out = run([oracle_bin("synth"), str(trip), "8", "1", str(thresh), "0", str(seed), tmp_path / "x.bin",
+               tmp_path / "z.bin"])
+    assert out.strip() == "rpc 0"
+    z = np.fromfile(tmp_path / "z.bin")
+    n_div = 0
+    for i in range(trip):
+        v = _f32(_f32(x[i]) * _f32(1.0001) + 0.5)
+        if (_mix((seed + i * 0x9E3779B97F4A7C15) & MASK) & 0xFFFFFFFF) < thresh:
+            v = _f32(v * _f32(0.9999) - 0.25)
+            n_div += 1
+        assert z[i] == v, i
+    assert 0 < n_div < trip
+
+
 # ------------------------------------------------------------------ spmv_serve
 
 def test_spmv_serve_oracle_hand_case(oracle_bin, tmp_path, monkeypatch):
     """A 3x3 matrix, two passes, one request of each kind checked by hand."""
+    monkeypatch.setenv("GF_SERVE_VAR0", "zz")               # set, so that the name's index matters
     monkeypatch.setenv("GF_SERVE_VAR1", "abc")
     monkeypatch.delenv("GF_SERVE_VAR2", raising=False)
     rowptr = np.array([0, 2, 3, 4], dtype=np.int64)
