@@ -20,7 +20,8 @@
  *   bulkchunks large fwrites in chunks mapped once, and writes cut short
  *   closerace  fclose while other producers write and flush the same file
  *   retire     mappings of finished large writes while no server thread goes
- *              idle: at most 16 are kept, closing the server releases the rest
+ *              idle: at most 16 are kept, stale ones are released by any idle
+ *              thread, closing the server releases the rest
  */
 #include <stdio.h>
 #include <stdlib.h>
@@ -499,10 +500,24 @@ int main(int argc, char **argv)
         }
         if (maps() != 16)
             return fail("the 16 latest finished writes are not kept mapped");
-        S.join();                                   /* close_all releases them */
+        /* older than the stale limit, they are released by any thread that
+         * calls idle(), here one that served nothing */
+        std::this_thread::sleep_for(std::chrono::milliseconds(60));
+        for (int k = 20; k < 22; k++) {              /* two fresh ones, which stay */
+            const std::string path = base + std::to_string(k);
+            const int64_t fh = call1(R, GF_OP_FOPEN, {{'s', 0, path + '\0'}, {'s', 0, std::string("wb") + '\0'}});
+            if (!fh || call1(R, GF_OP_FWRITE, {{'L', 1, ""}, {'L', C, ""}, {'L', (uint64_t)fh, ""}, {'A', 0, ""},
+                                               {'L', C, ""}, {'L', C, ""}}) != (int64_t)C ||
+                call1(R, GF_OP_FCLOSE, {{'L', (uint64_t)fh, ""}}) != 0)
+                return fail("fresh write");
+        }
+        S.srv.idle();
+        if (maps() > 2)
+            return fail("stale mappings not released by an idle thread");
+        S.join();                                   /* close_all releases the rest */
         if (maps() != 0)
             return fail("mappings left after close_all");
-        for (int k = 0; k < 20; k++) {
+        for (int k = 0; k < 22; k++) {
             const std::string path = base + std::to_string(k);
             FILE *in = fopen(path.c_str(), "rb");
             std::vector<uint8_t> got(C + 1);
